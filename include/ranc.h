@@ -1,0 +1,205 @@
+/*
+ * ranc.h - C ABI of the GB300 (sm_103a) RANC tick simulator.
+ *
+ * The library simulates the per-tick update of every neuromorphic core of a
+ * RANC grid (GPU-RANC, arXiv 2404.16208, Alg. 1 and Sec. III): each core
+ * reads its active axons from a 16-row scheduler, integrates them through a
+ * binary axon x neuron crossbar with one weight per (axon type, neuron), then
+ * every neuron applies leak, positive and negative thresholds and reset, and
+ * spiking neurons send packets (dx, dy, axon, delay) into row (tick + delay)
+ * mod 16 of the destination core's scheduler or count on the output bus.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: RANC_OK (0) or a negative RANC_E* code; the reason is
+ *     available from ranc_last_error().  No C++ exception crosses the ABI.
+ *   - A CUDA failure (RANC_ECUDA, RANC_ETIMEOUT) makes the handle sticky-failed:
+ *     every later call except ranc_reset/ranc_destroy/ranc_last_error returns
+ *     RANC_ESTATE until ranc_reset() succeeds.
+ *   - All work is ordered on the CUDA stream given to ranc_create (NULL = the
+ *     legacy default stream).  Entry points that write host memory synchronise
+ *     that stream before returning; the others only enqueue work.
+ *   - "host" pointers are ordinary (pageable or pinned) host memory owned by
+ *     the caller; "device" pointers are CUDA device memory owned by the
+ *     caller.  The library owns every allocation it makes and frees it in
+ *     ranc_destroy().  Nothing the caller passes is retained after a call
+ *     returns.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ *   - Samples are independent copies of the network (a batch); sample b of
+ *     every array below is the b-th sample.
+ */
+#ifndef RANC_H
+#define RANC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RANC_OK 0
+#define RANC_EINVAL (-1)   /* invalid argument or network description */
+#define RANC_ENOMEM (-2)   /* device or host allocation failed */
+#define RANC_ECUDA (-3)    /* a CUDA runtime call or kernel failed */
+#define RANC_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define RANC_ESTATE (-5)   /* call not valid in the handle's state */
+
+#define RANC_ROWS 16 /* scheduler rows per core: legal delays are 1..15 */
+
+/* Destination kinds of a neuron's spike packet (Sec. III-D). */
+enum { RANC_DEST_NONE = 0, RANC_DEST_CORE = 1, RANC_DEST_OUTPUT = 2 };
+/* What a potential below the negative threshold becomes. */
+enum { RANC_NEG_SATURATE = 0, RANC_NEG_RESET = 1 };
+/* Execution path.  PLAIN: one thread per neuron, bit-parallel crossbar
+ * integration, any batch.  BATCHED: many samples per core at once, crossbar
+ * integration as a tensor-core GEMM (tcgen05) per core; batch is padded
+ * internally to a multiple of 128 samples. */
+enum { RANC_PATH_PLAIN = 0, RANC_PATH_BATCHED = 1 };
+/* Where the buffers of ranc_run_samples live. */
+enum { RANC_MEM_HOST = 0, RANC_MEM_DEVICE = 1 };
+/* Indices of the counters returned by ranc_read_counters. */
+enum {
+    RANC_CNT_SPIKES = 0,   /* neurons that fired */
+    RANC_CNT_PACKETS = 1,  /* packets delivered to a core (one per kind-core spike) */
+    RANC_CNT_OUTPUTS = 2,  /* output-bus events (one per kind-output spike) */
+    RANC_CNT_SYNAPTIC = 3, /* (axon, neuron) pairs with an active axon and a connection */
+    RANC_CNT_TICKS = 4,    /* sample-ticks simulated (ticks x batch) */
+    RANC_N_COUNTERS = 5
+};
+
+/* Spike packet of one neuron (Sec. III-D: destination core as an offset,
+ * target tick offset and destination axon).  kind = CORE: the packet goes to
+ * the core at (x + dx, y + dy), axon `axon`, delay ticks later (1..15).
+ * kind = OUTPUT: one output-bus event with id `axon`.  kind = NONE: dropped. */
+typedef struct {
+    int16_t dx, dy;
+    uint16_t axon;
+    uint8_t delay, kind;
+} ranc_dest;
+
+/* Network / core-parameter description (Sec. II: axons, neurons, synaptic
+ * connections, axon types with one weight per type per neuron, CSRAM
+ * parameters; Sec. III-B: the per-neuron parameters as one contiguous array).
+ * Every array is host memory owned by the caller and read only during
+ * ranc_create.  C = n_cores, A = axons, N = neurons, K = n_types.
+ *   grid_w, grid_h  mesh size; core_xy[C][2] = (x, y), distinct, in the grid
+ *   axons, neurons  multiples of 32, 32..1024
+ *   n_types         1..8
+ *   weight_bits     2..12: every weight lies in +-(2^(weight_bits-1) - 1)
+ *   neg_mode        RANC_NEG_SATURATE or RANC_NEG_RESET
+ *   crossbar[C][A][N/32]   synapse (a, n) = bit n%32 of word n/32
+ *   axon_type[C][A]        in [0, K)
+ *   weight[C][K][N]
+ *   leak, pos_thr, neg_thr, reset, v0 [C][N]   (v0 = potential at reset)
+ *   dest[C][N]
+ *   n_inputs, n_outputs    input lines, output-bus ids (n_outputs >= 1)
+ *   in_offsets[n_inputs+1], in_core[nnz], in_axon[nnz]: input line i drives
+ *     (in_core[k], in_axon[k]) for k in [in_offsets[i], in_offsets[i+1])
+ * The update of a neuron is V <- V + sum of its active connected weights +
+ * leak; V >= pos_thr fires and sets V <- reset; otherwise V < neg_thr sets
+ * V <- neg_thr (SATURATE) or reset (RESET).  ranc_create rejects a description
+ * whose potential could leave int32. */
+typedef struct {
+    int32_t grid_w, grid_h, n_cores, axons, neurons, n_types, weight_bits, neg_mode;
+    const int16_t *core_xy;
+    const uint32_t *crossbar;
+    const uint8_t *axon_type;
+    const int16_t *weight;
+    const int32_t *leak, *pos_thr, *neg_thr, *reset, *v0;
+    const ranc_dest *dest;
+    int32_t n_inputs, n_outputs;
+    const int32_t *in_offsets, *in_core, *in_axon;
+} ranc_desc;
+
+typedef struct ranc_sim ranc_sim;
+
+/* Validate `desc`, copy it to the device in the layout of `path` and return a
+ * handle in *out with every sample at tick 0 (V = v0, empty scheduler, zero
+ * outputs and counters).  Sec. III-B/III-E: the CSRAM and scheduler arrays
+ * are allocated and copied to the device once.  `cuda_stream` is a
+ * cudaStream_t (NULL = default stream) used by every later call.
+ * Errors: RANC_EINVAL (bad description, batch < 1, unknown path, no sm_103
+ * device for the batched path), RANC_ENOMEM, RANC_ECUDA.  *out is NULL on
+ * error. */
+int ranc_create(const ranc_desc *desc, int32_t batch, int32_t path, void *cuda_stream, ranc_sim **out);
+
+/* Replace the input schedule with `bits` (host) [batch][n_ticks][ceil(n_inputs/32)]:
+ * line i of input tick j is bit i%32 of word i/32 and is written into the
+ * current scheduler row of the cores it drives at tick j counted from the last
+ * reset, before the neuron block (Alg. 1, packets of the current tick).
+ * Ticks at or beyond n_ticks carry no input.  n_ticks may be 0.  Synchronous. */
+int ranc_load_inputs(ranc_sim *sim, const uint32_t *bits, int32_t n_ticks);
+/* As ranc_load_inputs, with `bits` in device memory; stream-ordered, no sync. */
+int ranc_load_inputs_device(ranc_sim *sim, const uint32_t *bits, int32_t n_ticks);
+
+/* Advance every sample by n_ticks ticks (n_ticks >= 0), each tick a full pass
+ * of Alg. 1: scheduler row read and clear, input injection, crossbar
+ * integration, leak / threshold / reset, packet delivery and output-bus
+ * counting.  Stream-ordered; errors of the enqueued kernels surface at the
+ * next synchronising call. */
+int ranc_step(ranc_sim *sim, int32_t n_ticks);
+
+/* Output-bus counts since the last reset, [batch][n_outputs] uint32, into host
+ * memory (synchronous) or device memory (stream-ordered, no sync). */
+int ranc_read_outputs(ranc_sim *sim, uint32_t *counts);
+int ranc_read_outputs_device(ranc_sim *sim, uint32_t *counts);
+
+/* Host copies of the state after the last completed tick; each pointer may be
+ * NULL.  v [batch][C][N] int32 potentials; spikes [batch][C][N/32] (bit n%32
+ * of word n/32 = neuron n fired in the last tick); digest = sum over the flat
+ * index i = (b*C + c)*N + n of splitmix64_mix((i << 32) | (uint32)V_i)
+ * modulo 2^64, where splitmix64_mix is SplitMix64's output mixing function
+ * (order independent, so it is computed on the device).  Synchronous. */
+int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint64_t *digest);
+
+/* counters[RANC_N_COUNTERS] summed over the batch since the last ranc_reset
+ * (ranc_run_samples keeps accumulating across its windows).  Synchronous. */
+int ranc_read_counters(ranc_sim *sim, uint64_t *counters);
+
+/* Current tick (counted from the last reset) of every sample. */
+int ranc_get_tick(const ranc_sim *sim, int64_t *tick);
+
+/* Back to tick 0: V = v0, empty schedulers, zero outputs, zero counters,
+ * spike flags cleared; the input schedule is kept.  Clears a sticky failure
+ * when the device is still usable. */
+int ranc_reset(ranc_sim *sim);
+
+/* Run sample windows back to back: samples are taken `batch` at a time; each
+ * group is reset (counters excepted), given inputs[s][t_in][words] of its
+ * samples, stepped `window` ticks, and its output-bus counts are written to
+ * counts[s][n_outputs].  A last partial group leaves the unused samples
+ * without input and without output.  `mem` says whether `inputs` and `counts`
+ * are host (synchronous) or device (stream-ordered) memory.  Reading R7 of the
+ * sample window: every sample starts from V = v0 and empty schedulers. */
+int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in, int32_t window,
+                     uint32_t *counts, int32_t mem);
+
+/* Checkpoint.  ranc_save_state with buf == NULL stores the needed size in *n;
+ * otherwise *n must be at least that size and the state after the last
+ * completed tick (tick, V, schedulers, outputs, counters, last spikes) is
+ * written to buf (host).  ranc_load_state restores a buffer written by a
+ * handle with the same description shape, batch and path.  Synchronous. */
+int ranc_save_state(ranc_sim *sim, void *buf, size_t *n);
+int ranc_load_state(ranc_sim *sim, const void *buf, size_t n);
+
+/* Per-kernel timing of the tick kernels with CUDA events on the handle's
+ * stream (off by default).  ranc_read_kernel_timing returns the summed
+ * duration in milliseconds and the number of timed tick-kernel launches since
+ * timing was enabled; synchronous. */
+int ranc_set_kernel_timing(ranc_sim *sim, int32_t enable);
+int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
+
+/* Number of kernels this handle has launched since ranc_create. */
+int ranc_launch_count(const ranc_sim *sim, int64_t *launches);
+
+/* Free every device and host resource of the handle.  NULL is a no-op. */
+void ranc_destroy(ranc_sim *sim);
+
+/* Reason of the last failure on this handle, or of the last failed
+ * ranc_create when sim is NULL.  Never NULL; valid until the next call. */
+const char *ranc_last_error(const ranc_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RANC_H */

@@ -1,0 +1,718 @@
+// Host implementation of the C ABI declared in include/ranc.h.
+//
+// ranc_create validates the network description, lays it out for the chosen
+// path and copies it to the device once (Sec. III-B: the CSRAM becomes one
+// contiguous array copied once; Sec. III-E: the schedulers of all cores become
+// one array).  Every later call only launches kernels or copies state.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ranc_internal.cuh"
+#include "ranc_ptx.cuh"
+
+using namespace ranc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(ranc_sim *sim, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (sim) {
+        sim->last_error = buf;
+        if (code == RANC_ECUDA || code == RANC_ETIMEOUT) sim->sticky = 1;
+    } else {
+        g_create_error = buf;
+    }
+    return code;
+}
+
+#define CUDA_OR_FAIL(sim, expr)                                                                  \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail((sim), RANC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CHECK_LIVE(sim)                                                                          \
+    do {                                                                                         \
+        if (!(sim)) return RANC_EINVAL;                                                          \
+        if ((sim)->sticky) return fail((sim), RANC_ESTATE, "handle failed earlier: %s; call ranc_reset", \
+                                       (sim)->last_error.c_str());                               \
+    } while (0)
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T **p, const std::vector<T> &h) {
+    cudaError_t e = dmalloc(p, h.size());
+    if (e != cudaSuccess) return e;
+    if (h.empty()) return cudaSuccess;
+    return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+bool bad(std::string &why, const char *fmt, ...) {
+    char buf[400];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    why = buf;
+    return false;
+}
+
+// Checks every rule stated for ranc_desc; fills core_at (grid cell -> core).
+bool validate(const ranc_desc *d, int batch, int path, std::vector<int> &core_at, std::string &why) {
+    if (!d) return bad(why, "desc is NULL");
+    if (batch < 1) return bad(why, "batch must be >= 1 (got %d)", batch);
+    if (path != RANC_PATH_PLAIN && path != RANC_PATH_BATCHED) return bad(why, "unknown path %d", path);
+    if (d->n_cores < 1) return bad(why, "n_cores must be >= 1");
+    if (d->axons < 32 || d->axons > 1024 || d->axons % 32) return bad(why, "axons must be a multiple of 32 in [32, 1024]");
+    if (d->neurons < 32 || d->neurons > 1024 || d->neurons % 32)
+        return bad(why, "neurons must be a multiple of 32 in [32, 1024]");
+    if (d->n_types < 1 || d->n_types > kMaxTypes) return bad(why, "n_types must be in [1, %d]", kMaxTypes);
+    if (d->weight_bits < 2 || d->weight_bits > 12) return bad(why, "weight_bits must be in [2, 12]");
+    if (d->neg_mode != RANC_NEG_SATURATE && d->neg_mode != RANC_NEG_RESET) return bad(why, "unknown neg_mode");
+    if (d->grid_w < 1 || d->grid_h < 1 || (long long)d->grid_w * d->grid_h > (1 << 24)) return bad(why, "bad grid size");
+    if (d->n_inputs < 0 || d->n_outputs < 1) return bad(why, "n_inputs must be >= 0 and n_outputs >= 1");
+    if (!d->core_xy || !d->crossbar || !d->axon_type || !d->weight || !d->leak || !d->pos_thr || !d->neg_thr ||
+        !d->reset || !d->v0 || !d->dest || !d->in_offsets || (d->n_inputs > 0 && (!d->in_core || !d->in_axon)))
+        return bad(why, "a required array is NULL");
+    const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types;
+    core_at.assign((size_t)d->grid_w * d->grid_h, -1);
+    for (int c = 0; c < C; c++) {
+        const int x = d->core_xy[2 * c], y = d->core_xy[2 * c + 1];
+        if (x < 0 || x >= d->grid_w || y < 0 || y >= d->grid_h) return bad(why, "core %d at (%d,%d) is off the grid", c, x, y);
+        int &slot = core_at[(size_t)y * d->grid_w + x];
+        if (slot >= 0) return bad(why, "cores %d and %d share grid cell (%d,%d)", slot, c, x, y);
+        slot = c;
+    }
+    for (size_t i = 0; i < (size_t)C * A; i++)
+        if (d->axon_type[i] >= K) return bad(why, "axon_type[%zu] = %d is not < n_types", i, d->axon_type[i]);
+    const int wmax = (1 << (d->weight_bits - 1)) - 1;
+    for (size_t i = 0; i < (size_t)C * K * N; i++)
+        if (d->weight[i] > wmax || d->weight[i] < -wmax)
+            return bad(why, "weight[%zu] = %d is outside +-%d (weight_bits %d)", i, d->weight[i], wmax, d->weight_bits);
+    for (int c = 0; c < C; c++) {
+        for (int n = 0; n < N; n++) {
+            const size_t i = (size_t)c * N + n;
+            const ranc_dest &t = d->dest[i];
+            if (t.kind == RANC_DEST_NONE) continue;
+            if (t.kind == RANC_DEST_OUTPUT) {
+                if (t.axon >= d->n_outputs) return bad(why, "core %d neuron %d: output id %d >= n_outputs", c, n, t.axon);
+                continue;
+            }
+            if (t.kind != RANC_DEST_CORE) return bad(why, "core %d neuron %d: unknown destination kind %d", c, n, t.kind);
+            if (t.delay < 1 || t.delay >= kRows) return bad(why, "core %d neuron %d: delay %d not in [1, 15]", c, n, t.delay);
+            if (t.axon >= A) return bad(why, "core %d neuron %d: destination axon %d >= axons", c, n, t.axon);
+            const int x = d->core_xy[2 * c] + t.dx, y = d->core_xy[2 * c + 1] + t.dy;
+            if (x < 0 || x >= d->grid_w || y < 0 || y >= d->grid_h || core_at[(size_t)y * d->grid_w + x] < 0)
+                return bad(why, "core %d neuron %d: destination (%d,%d) is not a core", c, n, x, y);
+        }
+        // Potential range (int32 safety): after any tick V lies in
+        // [min(neg_thr, reset), max(pos_thr - 1, reset)] or is v0.
+        for (int n = 0; n < N; n++) {
+            const size_t i = (size_t)c * N + n;
+            long long hi = std::max({(long long)d->pos_thr[i] - 1, (long long)d->reset[i], (long long)d->v0[i]});
+            long long lo = std::min({(long long)d->neg_thr[i], (long long)d->reset[i], (long long)d->v0[i]});
+            long long span = (long long)A * wmax + std::llabs((long long)d->leak[i]);
+            if (hi + span > INT32_MAX || lo - span < INT32_MIN)
+                return bad(why, "core %d neuron %d: the potential could leave int32", c, n);
+        }
+    }
+    if (d->in_offsets[0] != 0) return bad(why, "in_offsets[0] must be 0");
+    for (int i = 0; i < d->n_inputs; i++)
+        if (d->in_offsets[i + 1] < d->in_offsets[i]) return bad(why, "in_offsets must be non-decreasing");
+    for (int k = 0; k < (d->n_inputs > 0 ? d->in_offsets[d->n_inputs] : 0); k++) {
+        if (d->in_core[k] < 0 || d->in_core[k] >= C) return bad(why, "in_core[%d] = %d is not a core", k, d->in_core[k]);
+        if (d->in_axon[k] < 0 || d->in_axon[k] >= A) return bad(why, "in_axon[%d] = %d is not an axon", k, d->in_axon[k]);
+    }
+    return true;
+}
+
+void free_all(ranc_sim *s) {
+    void *ptrs[] = {s->xbarT, s->tmask, s->wnk, s->prm, s->dst, s->in_ptr, s->in_line, s->in_axon, s->v0,
+                    s->V, s->ring, s->spk, s->out, s->cnt, s->inputs, s->err, s->digest, s->stage};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    batched_teardown(s);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    s->ev_pool.clear();
+}
+
+// Synchronises the stream and reads the device error word; returns a RANC code.
+int check_device_error(ranc_sim *sim) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, sim->err, sizeof(int), cudaMemcpyDeviceToHost, sim->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "kernel failure: %s", cudaGetErrorString(e));
+    if (h == kErrTimeout) return fail(sim, RANC_ETIMEOUT, "a device-side wait gave up after %llu ns", kWaitLimitNs);
+    if (h != kErrNone) return fail(sim, RANC_ECUDA, "device error code %d", h);
+    return RANC_OK;
+}
+
+int sync_and_check(ranc_sim *sim) { return check_device_error(sim); }
+
+
+int reset_state(ranc_sim *sim, bool counters) {
+    cudaError_t e = sim->path == RANC_PATH_PLAIN ? launch_plain_reset(sim, counters) : launch_batched_reset(sim, counters);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "reset: %s", cudaGetErrorString(e));
+    sim->tick = 0;
+    if (counters) sim->ticks_total = 0;
+    return RANC_OK;
+}
+
+cudaEvent_t next_event(ranc_sim *sim) {
+    if (sim->ev_used == (int)sim->ev_pool.size()) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+        sim->ev_pool.push_back(ev);
+    }
+    return sim->ev_pool[sim->ev_used++];
+}
+
+// Folds the recorded event pairs into timed_ms (synchronises the stream).
+int fold_timing(ranc_sim *sim) {
+    if (sim->ev_used == 0) return RANC_OK;
+    CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+    for (int i = 0; i + 1 < sim->ev_used; i += 2) {
+        float ms = 0.f;
+        CUDA_OR_FAIL(sim, cudaEventElapsedTime(&ms, sim->ev_pool[i], sim->ev_pool[i + 1]));
+        sim->timed_ms += ms;
+        sim->timed_launches++;
+    }
+    sim->ev_used = 0;
+    return RANC_OK;
+}
+
+int step_ticks(ranc_sim *sim, int n_ticks) {
+    for (int t = 0; t < n_ticks; t++) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (sim->timing) {
+            if (sim->ev_used + 2 > 4096) {
+                int rc = fold_timing(sim);
+                if (rc) return rc;
+            }
+            e0 = next_event(sim);
+            e1 = next_event(sim);
+            if (!e0 || !e1) return fail(sim, RANC_ECUDA, "cudaEventCreate failed");
+            CUDA_OR_FAIL(sim, cudaEventRecord(e0, sim->stream));
+        }
+        cudaError_t e;
+        if (sim->path == RANC_PATH_PLAIN) {
+            PlainArgs a{};
+            a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
+            a.B = sim->B; a.n_valid = sim->n_valid; a.in_words = sim->in_words; a.in_ticks = sim->in_ticks;
+            a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = sim->tick;
+            a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+            a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon;
+            a.inputs = sim->in_override ? sim->in_override : sim->inputs;
+            a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+            e = launch_plain_tick(a, sim->stream);
+        } else {
+            BatchedArgs a{};
+            a.tick = sim->tick;
+            e = launch_batched_tick(sim, a);
+        }
+        sim->launches++;
+        if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "tick kernel launch: %s", cudaGetErrorString(e));
+        if (sim->timing) CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+        sim->tick++;
+        sim->ticks_total += (unsigned long long)sim->n_valid;
+    }
+    return RANC_OK;
+}
+
+int ensure_inputs(ranc_sim *sim, size_t words) {
+    if (words <= sim->inputs_cap) return RANC_OK;
+    if (sim->inputs) {
+        CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+        cudaFree(sim->inputs);
+        sim->inputs = nullptr;
+        sim->inputs_cap = 0;
+    }
+    if (dmalloc(&sim->inputs, words) != cudaSuccess) return fail(sim, RANC_ENOMEM, "input buffer of %zu words", words);
+    sim->inputs_cap = words;
+    return RANC_OK;
+}
+
+// Installs inputs for samples [0, n_samples) of the batch (device pointer).
+int load_inputs_dev(ranc_sim *sim, const uint32_t *bits, int n_samples, int n_ticks) {
+    sim->in_override = nullptr;
+    sim->in_ticks = n_ticks;
+    sim->n_valid = n_samples;
+    if (n_ticks == 0) return RANC_OK;
+    if (sim->path == RANC_PATH_PLAIN) {
+        const size_t words = (size_t)sim->B * n_ticks * sim->in_words;
+        int rc = ensure_inputs(sim, words);
+        if (rc) return rc;
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->inputs, bits, (size_t)n_samples * n_ticks * sim->in_words * 4,
+                                          cudaMemcpyDeviceToDevice, sim->stream));
+        return RANC_OK;
+    }
+    cudaError_t e = launch_batched_inputs(sim, bits, n_samples, n_ticks);
+    if (e == cudaErrorMemoryAllocation) return fail(sim, RANC_ENOMEM, "batched input buffers");
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "batched input load: %s", cudaGetErrorString(e));
+    return RANC_OK;
+}
+
+int ensure_stage(ranc_sim *sim, size_t words) {
+    if (words <= sim->stage_cap) return RANC_OK;
+    if (sim->stage) {
+        CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+        cudaFree(sim->stage);
+        sim->stage = nullptr;
+        sim->stage_cap = 0;
+    }
+    if (dmalloc(&sim->stage, words) != cudaSuccess) return fail(sim, RANC_ENOMEM, "staging buffer of %zu words", words);
+    sim->stage_cap = words;
+    return RANC_OK;
+}
+
+int load_inputs_host(ranc_sim *sim, const uint32_t *bits, int n_samples, int n_ticks) {
+    const size_t words = (size_t)n_samples * n_ticks * sim->in_words;
+    if (words == 0) return load_inputs_dev(sim, nullptr, n_samples, 0);
+    int rc = ensure_stage(sim, words);
+    if (rc) return rc;
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->stage, bits, words * 4, cudaMemcpyHostToDevice, sim->stream));
+    rc = load_inputs_dev(sim, sim->stage, n_samples, n_ticks);
+    if (rc) return rc;
+    CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+    return RANC_OK;
+}
+
+size_t ring_words(const ranc_sim *s) { return (size_t)s->B * s->C * kRows * (s->A / 32); }
+
+// Canonical state views (plain layout) for read_state / save / load.  For the
+// batched path the state is converted by kernels into temporary buffers.
+struct Canon {
+    int *V = nullptr;
+    uint32_t *spk = nullptr, *ring = nullptr;
+    bool owned = false;
+    ~Canon() {
+        if (owned) {
+            cudaFree(V);
+            cudaFree(spk);
+            cudaFree(ring);
+        }
+    }
+};
+
+int canon_view(ranc_sim *sim, Canon &cv, bool need_ring) {
+    if (sim->path == RANC_PATH_PLAIN) {
+        cv.V = (int *)sim->V;
+        cv.spk = sim->spk;
+        cv.ring = sim->ring;
+        return RANC_OK;
+    }
+    cv.owned = true;
+    if (dmalloc(&cv.V, (size_t)sim->B * sim->C * sim->N) != cudaSuccess ||
+        dmalloc(&cv.spk, (size_t)sim->B * sim->C * (sim->N / 32)) != cudaSuccess ||
+        (need_ring && dmalloc(&cv.ring, ring_words(sim)) != cudaSuccess))
+        return fail(sim, RANC_ENOMEM, "temporary state buffers");
+    cudaError_t e = launch_batched_export(sim, cv.V, cv.spk, need_ring ? cv.ring : nullptr);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state export: %s", cudaGetErrorString(e));
+    return RANC_OK;
+}
+
+struct SaveHeader {
+    char magic[8];
+    int32_t version, C, A, N, B, path, n_outputs, pad;
+    int64_t tick;
+    uint64_t ticks_total;
+};
+
+size_t save_size(const ranc_sim *s) {
+    return sizeof(SaveHeader) + (size_t)s->B * s->C * s->N * 4 + ring_words(s) * 4 + (size_t)s->B * s->n_outputs * 4 +
+           (size_t)s->B * s->C * (s->N / 32) * 4 + 4 * 8;
+}
+
+__global__ void reduce_counters_kernel(const unsigned long long *cnt, long long rows, unsigned long long *out) {
+    unsigned long long acc[4] = {0, 0, 0, 0};
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
+        for (int j = 0; j < 4; j++) acc[j] += cnt[r * 4 + j];
+    for (int j = 0; j < 4; j++) {
+        unsigned long long v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(out + j, v);
+    }
+}
+
+int read_counters4(ranc_sim *sim, unsigned long long *h4) {
+    CUDA_OR_FAIL(sim, cudaMemsetAsync(sim->digest, 0, 5 * 8, sim->stream));
+    const long long rows = (long long)(sim->cnt_len / 4);
+    long long blocks = std::min<long long>((rows + 255) / 256, 1024);
+    if (blocks < 1) blocks = 1;
+    reduce_counters_kernel<<<(unsigned)blocks, 256, 0, sim->stream>>>(sim->cnt, rows, sim->digest + 1);
+    sim->launches++;
+    CUDA_OR_FAIL(sim, cudaGetLastError());
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(h4, sim->digest + 1, 4 * 8, cudaMemcpyDeviceToHost, sim->stream));
+    return sync_and_check(sim);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void *cuda_stream, ranc_sim **out) {
+    if (!out) return fail(nullptr, RANC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::vector<int> core_at;
+    std::string why;
+    if (!validate(d, batch, path, core_at, why)) return fail(nullptr, RANC_EINVAL, "%s", why.c_str());
+    ranc_sim *sim = new (std::nothrow) ranc_sim();
+    if (!sim) return fail(nullptr, RANC_ENOMEM, "host allocation");
+    const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types, AW = A / 32;
+    sim->C = C; sim->A = A; sim->N = N; sim->K = K; sim->B = batch; sim->path = path; sim->neg_mode = d->neg_mode;
+    sim->grid_w = d->grid_w; sim->grid_h = d->grid_h; sim->n_inputs = d->n_inputs; sim->n_outputs = d->n_outputs;
+    sim->in_words = (d->n_inputs + 31) / 32; sim->weight_bits = d->weight_bits;
+    sim->stream = static_cast<cudaStream_t>(cuda_stream);
+    sim->n_valid = batch;
+    auto abort_create = [&](int code, const std::string &msg) {
+        g_create_error = msg;
+        free_all(sim);
+        delete sim;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&sim->device);
+    if (e != cudaSuccess) return abort_create(RANC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+
+    // Host-side layout of the constant arrays.
+    std::vector<uint32_t> xbarT((size_t)C * N * AW, 0u), tmask((size_t)C * K * AW, 0u);
+    std::vector<int16_t> wnk((size_t)C * N * kMaxTypes, 0);
+    std::vector<int4> prm((size_t)C * N);
+    std::vector<uint2> dst((size_t)C * N);
+    const int NWd = N / 32;
+    for (int c = 0; c < C; c++) {
+        for (int a = 0; a < A; a++) {
+            const uint32_t *src = d->crossbar + ((size_t)c * A + a) * NWd;
+            for (int n = 0; n < N; n++)
+                if ((src[n >> 5] >> (n & 31)) & 1u) xbarT[((size_t)c * N + n) * AW + (a >> 5)] |= 1u << (a & 31);
+            tmask[((size_t)c * K + d->axon_type[(size_t)c * A + a]) * AW + (a >> 5)] |= 1u << (a & 31);
+        }
+        for (int n = 0; n < N; n++) {
+            const size_t i = (size_t)c * N + n;
+            for (int k = 0; k < K; k++) wnk[i * kMaxTypes + k] = d->weight[((size_t)c * K + k) * N + n];
+            prm[i] = make_int4(d->leak[i], d->pos_thr[i], d->neg_thr[i], d->reset[i]);
+            const ranc_dest &t = d->dest[i];
+            uint32_t target = 0;
+            if (t.kind == RANC_DEST_CORE)
+                target = (uint32_t)core_at[(size_t)(d->core_xy[2 * c + 1] + t.dy) * d->grid_w + (d->core_xy[2 * c] + t.dx)];
+            else if (t.kind == RANC_DEST_OUTPUT)
+                target = t.axon;
+            dst[i] = make_uint2(target, (uint32_t)t.axon | ((uint32_t)t.delay << 16) | ((uint32_t)t.kind << 24));
+        }
+    }
+    // Input fan-out regrouped per core: (line, axon) pairs.
+    std::vector<int> in_ptr(C + 1, 0), in_line, in_axon;
+    const int nnz = d->n_inputs > 0 ? d->in_offsets[d->n_inputs] : 0;
+    for (int k = 0; k < nnz; k++) in_ptr[d->in_core[k] + 1]++;
+    for (int c = 0; c < C; c++) in_ptr[c + 1] += in_ptr[c];
+    in_line.assign(nnz > 0 ? nnz : 1, 0);
+    in_axon.assign(nnz > 0 ? nnz : 1, 0);
+    {
+        std::vector<int> fill(in_ptr.begin(), in_ptr.end() - 1);
+        for (int i = 0; i < d->n_inputs; i++)
+            for (int k = d->in_offsets[i]; k < d->in_offsets[i + 1]; k++) {
+                const int p = fill[d->in_core[k]]++;
+                in_line[p] = i;
+                in_axon[p] = d->in_axon[k];
+            }
+    }
+    std::vector<int> v0(d->v0, d->v0 + (size_t)C * N);
+
+    if (upload(&sim->xbarT, xbarT) != cudaSuccess || upload(&sim->tmask, tmask) != cudaSuccess ||
+        upload(&sim->wnk, wnk) != cudaSuccess || upload(&sim->prm, prm) != cudaSuccess ||
+        upload(&sim->dst, dst) != cudaSuccess || upload(&sim->in_ptr, in_ptr) != cudaSuccess ||
+        upload(&sim->in_line, in_line) != cudaSuccess || upload(&sim->in_axon, in_axon) != cudaSuccess ||
+        upload(&sim->v0, v0) != cudaSuccess || dmalloc(&sim->err, 1) != cudaSuccess ||
+        dmalloc(&sim->digest, 8) != cudaSuccess)
+        return abort_create(RANC_ENOMEM, "device allocation of the network arrays failed");
+    if (cudaMemset(sim->err, 0, sizeof(int)) != cudaSuccess) return abort_create(RANC_ECUDA, "cudaMemset");
+
+    if (path == RANC_PATH_PLAIN) {
+        if (dmalloc((int **)&sim->V, (size_t)batch * C * N) != cudaSuccess ||
+            dmalloc(&sim->ring, (size_t)batch * C * kRows * AW) != cudaSuccess ||
+            dmalloc(&sim->spk, (size_t)batch * C * (N / 32)) != cudaSuccess ||
+            dmalloc(&sim->out, (size_t)batch * d->n_outputs) != cudaSuccess ||
+            dmalloc(&sim->cnt, (size_t)batch * C * 4) != cudaSuccess)
+            return abort_create(RANC_ENOMEM, "device allocation of the state arrays failed");
+        sim->cnt_len = (size_t)batch * C * 4;
+        e = plain_setup_kernel_attrs(N, AW);
+        if (e != cudaSuccess) return abort_create(RANC_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    } else {
+        e = batched_setup(sim, d, why);
+        if (e == cudaErrorInvalidValue) return abort_create(RANC_EINVAL, why);
+        if (e == cudaErrorMemoryAllocation) return abort_create(RANC_ENOMEM, why);
+        if (e != cudaSuccess) return abort_create(RANC_ECUDA, why + ": " + cudaGetErrorString(e));
+    }
+    int rc = reset_state(sim, true);
+    if (rc == RANC_OK) rc = sync_and_check(sim);
+    if (rc != RANC_OK) {
+        std::string msg = sim->last_error;
+        return abort_create(rc, msg);
+    }
+    *out = sim;
+    return RANC_OK;
+}
+
+extern "C" int ranc_load_inputs(ranc_sim *sim, const uint32_t *bits, int32_t n_ticks) {
+    CHECK_LIVE(sim);
+    if (n_ticks < 0 || (n_ticks > 0 && !bits)) return fail(sim, RANC_EINVAL, "bad input arguments");
+    return load_inputs_host(sim, bits, sim->B, n_ticks);
+}
+
+extern "C" int ranc_load_inputs_device(ranc_sim *sim, const uint32_t *bits, int32_t n_ticks) {
+    CHECK_LIVE(sim);
+    if (n_ticks < 0 || (n_ticks > 0 && !bits)) return fail(sim, RANC_EINVAL, "bad input arguments");
+    return load_inputs_dev(sim, bits, sim->B, n_ticks);
+}
+
+extern "C" int ranc_step(ranc_sim *sim, int32_t n_ticks) {
+    CHECK_LIVE(sim);
+    if (n_ticks < 0) return fail(sim, RANC_EINVAL, "n_ticks < 0");
+    return step_ticks(sim, n_ticks);
+}
+
+extern "C" int ranc_read_outputs(ranc_sim *sim, uint32_t *counts) {
+    CHECK_LIVE(sim);
+    if (!counts) return fail(sim, RANC_EINVAL, "counts is NULL");
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts, sim->out, (size_t)sim->B * sim->n_outputs * 4, cudaMemcpyDeviceToHost,
+                                      sim->stream));
+    return sync_and_check(sim);
+}
+
+extern "C" int ranc_read_outputs_device(ranc_sim *sim, uint32_t *counts) {
+    CHECK_LIVE(sim);
+    if (!counts) return fail(sim, RANC_EINVAL, "counts is NULL");
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts, sim->out, (size_t)sim->B * sim->n_outputs * 4,
+                                      cudaMemcpyDeviceToDevice, sim->stream));
+    return RANC_OK;
+}
+
+extern "C" int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint64_t *digest) {
+    CHECK_LIVE(sim);
+    Canon cv;
+    int rc = canon_view(sim, cv, false);
+    if (rc) return rc;
+    const size_t nv = (size_t)sim->B * sim->C * sim->N;
+    if (v) CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, cv.V, nv * 4, cudaMemcpyDeviceToHost, sim->stream));
+    if (spikes)
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, cv.spk, (size_t)sim->B * sim->C * (sim->N / 32) * 4,
+                                          cudaMemcpyDeviceToHost, sim->stream));
+    if (digest) {
+        cudaError_t e = launch_digest(cv.V, (long long)nv, sim->digest, sim->stream);
+        sim->launches++;
+        if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "digest: %s", cudaGetErrorString(e));
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(digest, sim->digest, 8, cudaMemcpyDeviceToHost, sim->stream));
+    }
+    return sync_and_check(sim);
+}
+
+extern "C" int ranc_read_counters(ranc_sim *sim, uint64_t *counters) {
+    CHECK_LIVE(sim);
+    if (!counters) return fail(sim, RANC_EINVAL, "counters is NULL");
+    unsigned long long h4[4];
+    int rc = read_counters4(sim, h4);
+    if (rc) return rc;
+    for (int j = 0; j < 4; j++) counters[j] = h4[j];
+    counters[RANC_CNT_TICKS] = sim->ticks_total;
+    return RANC_OK;
+}
+
+extern "C" int ranc_get_tick(const ranc_sim *sim, int64_t *tick) {
+    if (!sim || !tick) return RANC_EINVAL;
+    *tick = sim->tick;
+    return RANC_OK;
+}
+
+extern "C" int ranc_reset(ranc_sim *sim) {
+    if (!sim) return RANC_EINVAL;
+    if (sim->sticky) {
+        cudaError_t e = cudaStreamSynchronize(sim->stream);
+        if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "device unusable: %s", cudaGetErrorString(e));
+        cudaMemsetAsync(sim->err, 0, sizeof(int), sim->stream);
+        sim->sticky = 0;
+    }
+    sim->ev_used = 0;
+    sim->in_override = nullptr;
+    int rc = reset_state(sim, true);
+    if (rc) return rc;
+    return sync_and_check(sim);
+}
+
+extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in,
+                                int32_t window, uint32_t *counts, int32_t mem) {
+    CHECK_LIVE(sim);
+    if (n_samples < 0 || t_in < 0 || window < 0 || (n_samples > 0 && t_in > 0 && !inputs) ||
+        (n_samples > 0 && !counts) || (mem != RANC_MEM_HOST && mem != RANC_MEM_DEVICE))
+        return fail(sim, RANC_EINVAL, "bad run_samples arguments");
+    const size_t per = (size_t)t_in * sim->in_words;
+    for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
+        const int ns = std::min(sim->B, n_samples - s0);
+        int rc = reset_state(sim, false);
+        if (rc) return rc;
+        if (mem == RANC_MEM_DEVICE && sim->path == RANC_PATH_PLAIN && t_in > 0) {
+            sim->in_override = inputs + (size_t)s0 * per;  // read in place, no copy
+            sim->in_ticks = t_in;
+            sim->n_valid = ns;
+        } else if (mem == RANC_MEM_DEVICE) {
+            rc = load_inputs_dev(sim, t_in > 0 ? inputs + (size_t)s0 * per : nullptr, ns, t_in);
+        } else {
+            rc = load_inputs_host(sim, t_in > 0 ? inputs + (size_t)s0 * per : nullptr, ns, t_in);
+        }
+        if (rc) return rc;
+        rc = step_ticks(sim, window);
+        if (rc) return rc;
+        const size_t ob = (size_t)ns * sim->n_outputs * 4;
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts + (size_t)s0 * sim->n_outputs, sim->out, ob,
+                                          mem == RANC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                                          sim->stream));
+    }
+    sim->in_override = nullptr;
+    sim->n_valid = sim->B;
+    sim->in_ticks = 0;  // the window inputs are not kept as the handle's schedule
+    if (mem == RANC_MEM_HOST) return sync_and_check(sim);
+    return RANC_OK;
+}
+
+extern "C" int ranc_save_state(ranc_sim *sim, void *buf, size_t *n) {
+    CHECK_LIVE(sim);
+    if (!n) return fail(sim, RANC_EINVAL, "n is NULL");
+    const size_t need = save_size(sim);
+    if (!buf) {
+        *n = need;
+        return RANC_OK;
+    }
+    if (*n < need) return fail(sim, RANC_EINVAL, "buffer of %zu bytes < %zu", *n, need);
+    Canon cv;
+    int rc = canon_view(sim, cv, true);
+    if (rc) return rc;
+    SaveHeader h{};
+    memcpy(h.magic, "RANCSTA", 8);
+    h.version = 1; h.C = sim->C; h.A = sim->A; h.N = sim->N; h.B = sim->B; h.path = sim->path;
+    h.n_outputs = sim->n_outputs; h.tick = sim->tick; h.ticks_total = sim->ticks_total;
+    char *p = static_cast<char *>(buf);
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const size_t nv = (size_t)sim->B * sim->C * sim->N * 4, nr = ring_words(sim) * 4,
+                 no = (size_t)sim->B * sim->n_outputs * 4, ns = (size_t)sim->B * sim->C * (sim->N / 32) * 4;
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(p, cv.V, nv, cudaMemcpyDeviceToHost, sim->stream));
+    p += nv;
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(p, cv.ring, nr, cudaMemcpyDeviceToHost, sim->stream));
+    p += nr;
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(p, sim->out, no, cudaMemcpyDeviceToHost, sim->stream));
+    p += no;
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(p, cv.spk, ns, cudaMemcpyDeviceToHost, sim->stream));
+    p += ns;
+    unsigned long long h4[4];
+    rc = read_counters4(sim, h4);
+    if (rc) return rc;
+    memcpy(p, h4, sizeof h4);
+    *n = need;
+    return RANC_OK;
+}
+
+__global__ void load_counters_kernel(unsigned long long *cnt, unsigned long long c0, unsigned long long c1,
+                                     unsigned long long c2, unsigned long long c3) {
+    cnt[0] = c0;
+    cnt[1] = c1;
+    cnt[2] = c2;
+    cnt[3] = c3;
+}
+
+extern "C" int ranc_load_state(ranc_sim *sim, const void *buf, size_t n) {
+    CHECK_LIVE(sim);
+    if (!buf || n < save_size(sim)) return fail(sim, RANC_EINVAL, "state buffer too small");
+    SaveHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "RANCSTA", 8) != 0 || h.version != 1 || h.C != sim->C || h.A != sim->A || h.N != sim->N ||
+        h.B != sim->B || h.path != sim->path || h.n_outputs != sim->n_outputs)
+        return fail(sim, RANC_EINVAL, "state buffer does not match this handle");
+    const char *p = static_cast<const char *>(buf) + sizeof h;
+    const size_t nv = (size_t)sim->B * sim->C * sim->N * 4, nr = ring_words(sim) * 4,
+                 no = (size_t)sim->B * sim->n_outputs * 4, ns = (size_t)sim->B * sim->C * (sim->N / 32) * 4;
+    unsigned long long h4[4];
+    memcpy(h4, p + nv + nr + no + ns, sizeof h4);
+    if (sim->path == RANC_PATH_PLAIN) {
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->V, p, nv, cudaMemcpyHostToDevice, sim->stream));
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->ring, p + nv, nr, cudaMemcpyHostToDevice, sim->stream));
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->spk, p + nv + nr + no, ns, cudaMemcpyHostToDevice, sim->stream));
+    } else {
+        Canon cv;
+        cv.owned = true;
+        if (dmalloc(&cv.V, nv / 4) != cudaSuccess || dmalloc(&cv.ring, nr / 4) != cudaSuccess ||
+            dmalloc(&cv.spk, ns / 4) != cudaSuccess)
+            return fail(sim, RANC_ENOMEM, "temporary state buffers");
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(cv.V, p, nv, cudaMemcpyHostToDevice, sim->stream));
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(cv.ring, p + nv, nr, cudaMemcpyHostToDevice, sim->stream));
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->spk, p + nv + nr + no, ns, cudaMemcpyHostToDevice, sim->stream));
+        cudaError_t e = launch_batched_import(sim, cv.V, cv.ring);
+        if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state import: %s", cudaGetErrorString(e));
+        CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+    }
+    CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->out, p + nv + nr, no, cudaMemcpyHostToDevice, sim->stream));
+    // The partial counters collapse into row 0.
+    CUDA_OR_FAIL(sim, cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream));
+    load_counters_kernel<<<1, 1, 0, sim->stream>>>(sim->cnt, h4[0], h4[1], h4[2], h4[3]);
+    sim->launches++;
+    CUDA_OR_FAIL(sim, cudaGetLastError());
+    sim->tick = h.tick;
+    sim->ticks_total = h.ticks_total;
+    return sync_and_check(sim);
+}
+
+extern "C" int ranc_set_kernel_timing(ranc_sim *sim, int32_t enable) {
+    CHECK_LIVE(sim);
+    int rc = fold_timing(sim);
+    if (rc) return rc;
+    sim->timing = enable != 0;
+    sim->timed_ms = 0.0;
+    sim->timed_launches = 0;
+    return RANC_OK;
+}
+
+extern "C" int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches) {
+    CHECK_LIVE(sim);
+    int rc = fold_timing(sim);
+    if (rc) return rc;
+    if (total_ms) *total_ms = sim->timed_ms;
+    if (launches) *launches = sim->timed_launches;
+    return RANC_OK;
+}
+
+extern "C" int ranc_launch_count(const ranc_sim *sim, int64_t *launches) {
+    if (!sim || !launches) return RANC_EINVAL;
+    *launches = sim->launches;
+    return RANC_OK;
+}
+
+extern "C" void ranc_destroy(ranc_sim *sim) {
+    if (!sim) return;
+    cudaStreamSynchronize(sim->stream);
+    free_all(sim);
+    delete sim;
+}
+
+extern "C" const char *ranc_last_error(const ranc_sim *sim) {
+    if (!sim) return g_create_error.c_str();
+    return sim->last_error.c_str();
+}

@@ -1,0 +1,134 @@
+// Internal declarations of the RANC CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ranc.h"
+
+namespace ranc {
+
+constexpr int kRows = RANC_ROWS;     // scheduler rows (Sec. III-E); delays 1..15
+constexpr int kMaxTypes = 8;         // weight slots per neuron
+constexpr int kMaxWords = 32;        // axons/32 and neurons/32 upper bound (1024)
+constexpr int kTileS = 128;          // samples per tensor-core tile (batched path)
+
+// Device error word values (set by kernels, read by synchronous host calls).
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrBounds = 2 };
+
+// Resolved destination of a neuron: x = destination core (kind core) or output
+// id (kind output); y = axon | delay << 16 | kind << 24.
+__host__ __device__ inline uint32_t dest_axon(uint2 d) { return d.y & 0xFFFFu; }
+__host__ __device__ inline uint32_t dest_delay(uint2 d) { return (d.y >> 16) & 0xFFu; }
+__host__ __device__ inline uint32_t dest_kind(uint2 d) { return d.y >> 24; }
+
+// Per-launch parameters of the plain (one thread per neuron) tick kernel.
+struct PlainArgs {
+    int C, A, N, K, AW, NW, B;   // cores, axons, neurons, types, A/32, N/32, batch
+    int n_valid;                 // samples b < n_valid receive inputs
+    int in_words, in_ticks, n_out, neg_mode;
+    long long tick;              // tick being simulated (counted from reset)
+    const uint32_t *xbarT;       // [C][N][AW]   crossbar bits, one row of axon bits per neuron
+    const uint32_t *tmask;       // [C][K][AW]   axons of each type
+    const int16_t *wnk;          // [C][N][8]    weight per (neuron, type)
+    const int4 *prm;             // [C][N]       {leak, pos_thr, neg_thr, reset}
+    const uint2 *dst;            // [C][N]       resolved destination
+    const int *in_ptr;           // [C+1]        per-core list of (input line, axon)
+    const int *in_line, *in_axon;
+    const uint32_t *inputs;      // [B][in_ticks][in_words]
+    int *V;                      // [B][C][N]
+    uint32_t *ring;              // [B][C][kRows][AW]
+    uint32_t *spk;               // [B][C][NW]   spikes of the last tick
+    uint32_t *out;               // [B][n_out]
+    unsigned long long *cnt;     // [B][C][4]    spikes, packets, outputs, synaptic events
+    int *err;
+};
+
+// Batched-path device layout (one tile = kTileS samples, sample-minor bits).
+struct BatchedArgs {
+    int C, A, N, AW, T;          // cores, axons, neurons, A/32, number of sample tiles
+    int n_valid;                 // real samples (the rest of the last tile is padding)
+    int in_words, in_ticks, n_out, neg_mode;
+    long long tick;
+    const int4 *prm;             // [C][N]
+    const uint2 *dst;            // [C][N]
+    const int *in_ptr, *in_line, *in_axon;   // per-core (line, axon) lists
+    const uint32_t *inT;         // [T][in_ticks][n_inputs][4] sample-minor input bits
+    int n_inputs;
+    const uint32_t *xbarT;       // [C][N][AW] (synaptic-event count)
+    void *V;                     // [T][C][N/32][kTileS][32] int16 or int32
+    uint32_t *ring;              // [T][C][kRows][A][4] sample-minor scheduler rows
+    uint32_t *out;               // [B_pad][n_out]
+    unsigned long long *cnt;     // [T][C][4]
+    int *err;
+};
+
+}  // namespace ranc
+
+// Host-side handle.
+struct ranc_sim {
+    // shape
+    int C = 0, A = 0, N = 0, K = 0, B = 0, path = 0, neg_mode = 0;
+    int grid_w = 0, grid_h = 0, n_inputs = 0, n_outputs = 0, in_words = 0, weight_bits = 0;
+    int B_pad = 0, T = 0, v16 = 0;      // batched path: padded batch, tiles, int16 potentials
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // constant network arrays (device)
+    uint32_t *xbarT = nullptr, *tmask = nullptr;
+    int16_t *wnk = nullptr;
+    int4 *prm = nullptr;
+    uint2 *dst = nullptr;
+    int *in_ptr = nullptr, *in_line = nullptr, *in_axon = nullptr;
+    int *v0 = nullptr;
+    void *wfold = nullptr;              // batched: [C][N][A] fp16 folded weights
+    void *tmap = nullptr;               // batched: CUtensorMap storage (host)
+
+    // state (device)
+    void *V = nullptr;
+    uint32_t *ring = nullptr, *spk = nullptr, *out = nullptr;
+    unsigned long long *cnt = nullptr;  // per (sample or tile, core) partial counters
+    size_t cnt_len = 0;
+    uint32_t *inputs = nullptr;         // plain: [B][ticks][words]; batched: [T][ticks][n_inputs][4]
+    size_t inputs_cap = 0;
+    int in_ticks = 0;
+    const uint32_t *in_override = nullptr;  // plain: caller's device slice used by run_samples
+    uint32_t *stage = nullptr;          // batched: staging buffer for untransposed inputs
+    size_t stage_cap = 0;
+    int *err = nullptr;
+    unsigned long long *digest = nullptr;
+    int n_valid = 0;
+
+    long long tick = 0;
+    unsigned long long ticks_total = 0;  // RANC_CNT_TICKS
+    long long launches = 0;
+
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_launches = 0;
+
+    int sticky = 0;
+    std::string last_error;
+};
+
+namespace ranc {
+// Implemented in ranc_plain.cu
+cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s);
+cudaError_t plain_setup_kernel_attrs(int N, int AW);
+cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);
+cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s);
+// Implemented in ranc_batched.cu
+cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
+cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
+cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
+cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
+cudaError_t launch_batched_export(ranc_sim *sim, int *v_canon, uint32_t *spk_canon, uint32_t *ring_canon);
+cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *ring_canon);
+void batched_teardown(ranc_sim *sim);
+}  // namespace ranc

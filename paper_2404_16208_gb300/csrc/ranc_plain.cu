@@ -1,0 +1,189 @@
+// Plain path: one CTA per (core, sample), one thread per neuron.
+//
+// One launch is one tick of Alg. 1 for every core of every sample:
+//   1. scheduler row (tick mod 16) read and cleared (Sec. III-E);
+//   2. input lines of this tick ORed into that row (Alg. 1, packets of the
+//      current tick);
+//   3. crossbar integration (Alg. 1 neuron block; Sec. III-C): the core's
+//      bit-packed crossbar is staged into shared memory by one bulk copy of
+//      the TMA engine, overlapped with steps 1-2; each neuron ANDs the active
+//      axon bits with its row of connection bits and counts, per axon type,
+//      the surviving bits with popc, so dV = sum_k w[k] * count_k;
+//   4. leak, positive / negative threshold and reset;
+//   5. spikes compacted with one warp ballot per 32 neurons; kind-core spikes
+//      delivered with atomicOr into row (tick + delay) mod 16 of the
+//      destination scheduler (Sec. III-D), kind-output spikes counted on the
+//      output bus.
+// Rows written at tick t are t+1..t+15 (mod 16), never the row being read, so
+// the launch has no read/write race; OR and integer addition are order
+// independent, so the result does not depend on scheduling.
+
+#include "ranc_internal.cuh"
+#include "ranc_ptx.cuh"
+
+namespace ranc {
+
+__global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
+    extern __shared__ __align__(128) uint32_t xs[];  // [N][AW] crossbar rows of this core
+    __shared__ uint32_t s[kMaxWords];                 // active axons of this tick
+    __shared__ uint32_t tm[kMaxTypes * kMaxWords];    // axon-type masks
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[4];
+
+    const int c = blockIdx.x, b = blockIdx.y, n = threadIdx.x;
+    const int AW = a.AW, K = a.K, N = a.N;
+    const int lane = n & 31, warp = n >> 5;
+    const uint32_t xbytes = (uint32_t)N * AW * 4u;
+
+    if (n == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, xbytes);
+        bulk_g2s(xs, a.xbarT + (size_t)c * N * AW, xbytes, &bar);
+    }
+    const size_t bc = (size_t)b * a.C + c;
+    uint32_t *row = a.ring + (bc * kRows + (a.tick & (kRows - 1))) * AW;
+    if (n < AW) {
+        s[n] = row[n];
+        row[n] = 0u;
+    }
+    for (int i = n; i < K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c * K * AW + i];
+    if (n < 4) red[n] = 0u;
+    __syncthreads();
+
+    // Input lines of this tick (reading: input delay 0).
+    if (b < a.n_valid && a.tick < a.in_ticks) {
+        const uint32_t *in = a.inputs + ((size_t)b * a.in_ticks + a.tick) * a.in_words;
+        for (int k = a.in_ptr[c] + n; k < a.in_ptr[c + 1]; k += blockDim.x) {
+            const int L = a.in_line[k];
+            if ((in[L >> 5] >> (L & 31)) & 1u) {
+                const int ax = a.in_axon[k];
+                atomicOr(&s[ax >> 5], 1u << (ax & 31));
+            }
+        }
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (n == 0) atomicExch(a.err, kErrTimeout);
+        mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
+        return;
+    }
+
+    // Crossbar integration: count active, connected axons per type.
+    const uint32_t *xr = xs + (size_t)n * AW;
+    uint32_t cntk[kMaxTypes];
+#pragma unroll
+    for (int k = 0; k < kMaxTypes; ++k) cntk[k] = 0u;
+    uint32_t syn = 0u;
+    for (int w = 0; w < AW; ++w) {
+        const uint32_t sw = s[w];
+        if (sw == 0u) continue;  // uniform across the CTA
+        const uint32_t x = sw & xr[w];
+        syn += __popc(x);
+#pragma unroll
+        for (int k = 0; k < kMaxTypes; ++k)
+            if (k < K) cntk[k] += __popc(x & tm[k * AW + w]);
+    }
+    const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
+    const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
+    int dv = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxTypes; ++k)
+        if (k < K) dv += (int)(int16_t)(wr[k >> 1] >> (16 * (k & 1))) * (int)cntk[k];
+
+    // Leak, thresholds, reset.
+    const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
+    int *vp = a.V + bc * N + n;
+    int v = *vp + dv + pr.x;
+    const bool fire = v >= pr.y;
+    if (fire)
+        v = pr.w;
+    else if (v < pr.z)
+        v = a.neg_mode ? pr.w : pr.z;
+    *vp = v;
+
+    // Spike compaction and delivery.
+    const unsigned fm = __ballot_sync(0xffffffffu, fire);
+    if (lane == 0) a.spk[bc * a.NW + warp] = fm;
+    uint32_t kind = 0u;
+    if (fire) {
+        const uint2 d = a.dst[(size_t)c * N + n];
+        kind = dest_kind(d);
+        if (kind == RANC_DEST_CORE) {
+            const uint32_t ax = dest_axon(d);
+            const long long r = (a.tick + dest_delay(d)) & (kRows - 1);
+            atomicOr(a.ring + (((size_t)b * a.C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
+        } else if (kind == RANC_DEST_OUTPUT) {
+            atomicAdd(a.out + (size_t)b * a.n_out + d.x, 1u);
+        }
+    }
+    const unsigned pm = __ballot_sync(0xffffffffu, kind == RANC_DEST_CORE);
+    const unsigned om = __ballot_sync(0xffffffffu, kind == RANC_DEST_OUTPUT);
+    const unsigned sy = __reduce_add_sync(0xffffffffu, syn);
+    if (lane == 0) {
+        atomicAdd(&red[0], (uint32_t)__popc(fm));
+        atomicAdd(&red[1], (uint32_t)__popc(pm));
+        atomicAdd(&red[2], (uint32_t)__popc(om));
+        atomicAdd(&red[3], sy);
+    }
+    __syncthreads();
+    if (n < 4 && b < a.n_valid) a.cnt[bc * 4 + n] += red[n];
+}
+
+cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s) {
+    const size_t smem = (size_t)a.N * a.AW * 4;
+    plain_tick_kernel<<<dim3(a.C, a.B), a.N, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// V <- v0 for every sample.
+__global__ void plain_reset_v_kernel(int *V, const int *v0, long long per_sample, long long total) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        V[i] = v0[i % per_sample];
+}
+
+cudaError_t plain_setup_kernel_attrs(int N, int AW) {
+    const int smem = N * AW * 4;
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(plain_tick_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_plain_reset(ranc_sim *sim, bool counters) {
+    const long long per = (long long)sim->C * sim->N, total = per * sim->B;
+    cudaError_t e;
+    plain_reset_v_kernel<<<(unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096), 256, 0,
+                           sim->stream>>>((int *)sim->V, sim->v0, per, total);
+    sim->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t ring_bytes = (size_t)sim->B * sim->C * kRows * (sim->A / 32) * 4;
+    if ((e = cudaMemsetAsync(sim->ring, 0, ring_bytes, sim->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sim->spk, 0, (size_t)sim->B * sim->C * (sim->N / 32) * 4, sim->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B * sim->n_outputs * 4, sim->stream)) != cudaSuccess)
+        return e;
+    if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// Order-independent state digest: sum of splitmix64_mix((i << 32) | (uint32)V[i]).
+__global__ void digest_kernel(const int *V, long long n, unsigned long long *out) {
+    unsigned long long acc = 0ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += splitmix64_mix(((unsigned long long)i << 32) | (uint32_t)V[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    if (blocks < 1) blocks = 1;
+    digest_kernel<<<(unsigned)blocks, 256, 0, s>>>(V, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ranc

@@ -1,0 +1,259 @@
+"""Python binding of the RANC C ABI (``include/ranc.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+simulation work of its own; a failing call raises :class:`RancError` with the
+library's reason.  Importing this module loads ``_lib/libranc.so`` and fails
+loudly if it has not been built (``paper_2404_16208_gb300.build.build()``):
+there is no fallback.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libranc.so")
+
+RANC_OK, RANC_EINVAL, RANC_ENOMEM, RANC_ECUDA, RANC_ETIMEOUT, RANC_ESTATE = 0, -1, -2, -3, -4, -5
+RANC_PATH_PLAIN, RANC_PATH_BATCHED = 0, 1
+RANC_MEM_HOST, RANC_MEM_DEVICE = 0, 1
+COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
+EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
+            "ranc_read_outputs_device", "ranc_read_state", "ranc_read_counters", "ranc_get_tick", "ranc_reset",
+            "ranc_run_samples", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
+            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_destroy", "ranc_last_error")
+
+
+class RancError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"RANC error {code}: {msg}")
+        self.code = code
+
+
+class ranc_dest(C.Structure):
+    _fields_ = [("dx", C.c_int16), ("dy", C.c_int16), ("axon", C.c_uint16), ("delay", C.c_uint8),
+                ("kind", C.c_uint8)]
+
+
+class ranc_desc(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("grid_w", "grid_h", "n_cores", "axons", "neurons", "n_types",
+                                          "weight_bits", "neg_mode")] + [
+        ("core_xy", C.c_void_p), ("crossbar", C.c_void_p), ("axon_type", C.c_void_p), ("weight", C.c_void_p),
+        ("leak", C.c_void_p), ("pos_thr", C.c_void_p), ("neg_thr", C.c_void_p), ("reset", C.c_void_p),
+        ("v0", C.c_void_p), ("dest", C.c_void_p), ("n_inputs", C.c_int32), ("n_outputs", C.c_int32),
+        ("in_offsets", C.c_void_p), ("in_core", C.c_void_p), ("in_axon", C.c_void_p)]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libranc.so is not built at {path}; run paper_2404_16208_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i32, i64, u32p, u64p = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p
+    sig = {
+        "ranc_create": ([C.POINTER(ranc_desc), i32, i32, vp, C.POINTER(vp)], C.c_int),
+        "ranc_load_inputs": ([vp, u32p, i32], C.c_int),
+        "ranc_load_inputs_device": ([vp, vp, i32], C.c_int),
+        "ranc_step": ([vp, i32], C.c_int),
+        "ranc_read_outputs": ([vp, u32p], C.c_int),
+        "ranc_read_outputs_device": ([vp, vp], C.c_int),
+        "ranc_read_state": ([vp, vp, vp, u64p], C.c_int),
+        "ranc_read_counters": ([vp, u64p], C.c_int),
+        "ranc_get_tick": ([vp, C.POINTER(i64)], C.c_int),
+        "ranc_reset": ([vp], C.c_int),
+        "ranc_run_samples": ([vp, vp, i32, i32, i32, vp, i32], C.c_int),
+        "ranc_save_state": ([vp, vp, C.POINTER(C.c_size_t)], C.c_int),
+        "ranc_load_state": ([vp, vp, C.c_size_t], C.c_int),
+        "ranc_set_kernel_timing": ([vp, i32], C.c_int),
+        "ranc_read_kernel_timing": ([vp, C.POINTER(C.c_double), C.POINTER(i64)], C.c_int),
+        "ranc_launch_count": ([vp, C.POINTER(i64)], C.c_int),
+        "ranc_destroy": ([vp], None),
+        "ranc_last_error": ([vp], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(rc, h):
+    if rc != RANC_OK:
+        raise RancError(rc, _lib.ranc_last_error(h).decode())
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def ranc_create(net, batch, path=RANC_PATH_PLAIN, stream=0):
+    """Create a simulator for ``net`` (any object with the fields of a RANC
+    network description) and return the opaque handle."""
+    keep = [_c(net.core_xy, np.int16), _c(net.crossbar, np.uint32), _c(net.axon_type, np.uint8),
+            _c(net.weight, np.int16), _c(net.leak, np.int32), _c(net.pos_thr, np.int32),
+            _c(net.neg_thr, np.int32), _c(net.reset, np.int32), _c(net.v0, np.int32),
+            np.ascontiguousarray(net.dest), _c(net.in_offsets, np.int32), _c(net.in_core, np.int32),
+            _c(net.in_axon, np.int32)]
+    assert keep[9].dtype.itemsize == C.sizeof(ranc_dest)
+    d = ranc_desc(net.grid_w, net.grid_h, net.n_cores, net.axons, net.neurons, net.n_types, net.weight_bits,
+                  net.neg_mode, *[_p(a) for a in keep[:10]], net.n_inputs, net.n_outputs,
+                  *[_p(a) for a in keep[10:]])
+    h = C.c_void_p()
+    _check(_lib.ranc_create(C.byref(d), int(batch), int(path), C.c_void_p(int(stream)), C.byref(h)), None)
+    return h
+
+
+def ranc_load_inputs(h, bits):
+    """``bits``: host uint32 [batch, ticks, ceil(n_inputs/32)]."""
+    bits = _c(bits, np.uint32)
+    _check(_lib.ranc_load_inputs(h, _p(bits), int(bits.shape[1]) if bits.ndim == 3 else 0), h)
+
+
+def ranc_load_inputs_device(h, dev_ptr, n_ticks):
+    _check(_lib.ranc_load_inputs_device(h, C.c_void_p(int(dev_ptr)), int(n_ticks)), h)
+
+
+def ranc_step(h, n_ticks):
+    _check(_lib.ranc_step(h, int(n_ticks)), h)
+
+
+def ranc_read_outputs(h, batch, n_outputs):
+    out = np.zeros((batch, n_outputs), np.uint32)
+    _check(_lib.ranc_read_outputs(h, _p(out)), h)
+    return out
+
+
+def ranc_read_outputs_device(h, dev_ptr):
+    _check(_lib.ranc_read_outputs_device(h, C.c_void_p(int(dev_ptr))), h)
+
+
+def ranc_read_state(h, batch, n_cores, neurons, want_v=True, want_spikes=True, want_digest=True):
+    v = np.zeros((batch, n_cores, neurons), np.int32) if want_v else None
+    s = np.zeros((batch, n_cores, neurons // 32), np.uint32) if want_spikes else None
+    d = np.zeros(1, np.uint64)
+    _check(_lib.ranc_read_state(h, _p(v) if want_v else None, _p(s) if want_spikes else None,
+                                _p(d) if want_digest else None), h)
+    return v, s, (int(d[0]) if want_digest else None)
+
+
+def ranc_read_counters(h):
+    c = np.zeros(5, np.uint64)
+    _check(_lib.ranc_read_counters(h, _p(c)), h)
+    return c
+
+
+def ranc_get_tick(h):
+    t = C.c_int64()
+    _check(_lib.ranc_get_tick(h, C.byref(t)), h)
+    return t.value
+
+
+def ranc_reset(h):
+    _check(_lib.ranc_reset(h), h)
+
+
+def ranc_run_samples(h, inputs, n_samples, t_in, window, counts, mem=RANC_MEM_HOST):
+    """Host mode: ``inputs`` uint32 [S, t_in, words] and ``counts`` uint32
+    [S, n_outputs] numpy arrays.  Device mode: both are device pointers."""
+    if mem == RANC_MEM_HOST:
+        inputs = _c(inputs, np.uint32)
+        assert counts.dtype == np.uint32 and counts.flags.c_contiguous
+        ip, cp = _p(inputs), _p(counts)
+    else:
+        ip, cp = C.c_void_p(int(inputs)), C.c_void_p(int(counts))
+    _check(_lib.ranc_run_samples(h, ip, int(n_samples), int(t_in), int(window), cp, int(mem)), h)
+
+
+def ranc_save_state(h):
+    n = C.c_size_t(0)
+    _check(_lib.ranc_save_state(h, None, C.byref(n)), h)
+    buf = np.zeros(n.value, np.uint8)
+    _check(_lib.ranc_save_state(h, _p(buf), C.byref(n)), h)
+    return buf
+
+
+def ranc_load_state(h, buf):
+    buf = _c(buf, np.uint8)
+    _check(_lib.ranc_load_state(h, _p(buf), buf.size), h)
+
+
+def ranc_set_kernel_timing(h, enable):
+    _check(_lib.ranc_set_kernel_timing(h, 1 if enable else 0), h)
+
+
+def ranc_read_kernel_timing(h):
+    ms, n = C.c_double(), C.c_int64()
+    _check(_lib.ranc_read_kernel_timing(h, C.byref(ms), C.byref(n)), h)
+    return ms.value, n.value
+
+
+def ranc_launch_count(h):
+    n = C.c_int64()
+    _check(_lib.ranc_launch_count(h, C.byref(n)), h)
+    return n.value
+
+
+def ranc_destroy(h):
+    _lib.ranc_destroy(h)
+
+
+def ranc_last_error(h=None):
+    return _lib.ranc_last_error(h).decode()
+
+
+class Sim:
+    """Owning wrapper around one handle (same calls, shapes filled in)."""
+
+    def __init__(self, net, batch, path=RANC_PATH_PLAIN, stream=0):
+        self.net, self.batch, self.path = net, int(batch), path
+        self.h = ranc_create(net, batch, path, stream)
+
+    def load_inputs(self, bits):
+        ranc_load_inputs(self.h, bits)
+
+    def step(self, n_ticks):
+        ranc_step(self.h, n_ticks)
+
+    def outputs(self):
+        return ranc_read_outputs(self.h, self.batch, self.net.n_outputs)
+
+    def state(self, **kw):
+        return ranc_read_state(self.h, self.batch, self.net.n_cores, self.net.neurons, **kw)
+
+    def counters(self):
+        return ranc_read_counters(self.h)
+
+    def tick(self):
+        return ranc_get_tick(self.h)
+
+    def reset(self):
+        ranc_reset(self.h)
+
+    def run_samples(self, inputs, window):
+        inputs = _c(inputs, np.uint32)
+        counts = np.zeros((inputs.shape[0], self.net.n_outputs), np.uint32)
+        ranc_run_samples(self.h, inputs, inputs.shape[0], inputs.shape[1], window, counts)
+        return counts
+
+    def save(self):
+        return ranc_save_state(self.h)
+
+    def load(self, buf):
+        ranc_load_state(self.h, buf)
+
+    def close(self):
+        if self.h is not None:
+            ranc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

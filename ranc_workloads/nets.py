@@ -106,7 +106,7 @@ def make_net(name, grid_w, grid_h, core_xy, syn, axon_type, weight, leak, pos_th
     """
     syn = np.asarray(syn, dtype=np.uint8)
     C, A, N = syn.shape
-    as32 = lambda x: np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.int32), (C, N)))
+    as32 = lambda x: np.array(np.broadcast_to(np.asarray(x, dtype=np.int32), (C, N)), dtype=np.int32)
     offs, icore, iaxon = fanout_csr(n_inputs, fanout)
     return Net(
         name=name, grid_w=int(grid_w), grid_h=int(grid_h), axons=int(A), neurons=int(N),

@@ -1,0 +1,129 @@
+"""CPU-only checks of the C ABI: the library loads, exports every entry point
+that include/ranc.h declares, the binding's struct layouts match the C
+compiler's, and ranc_create's host-side validation rejects bad descriptions
+(validation runs before any CUDA call, so no GPU is needed)."""
+
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import ranc_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ranc.h")
+
+
+@pytest.fixture(scope="module")
+def ranc():
+    from paper_2404_16208_gb300 import build_library
+    build_library()
+    from paper_2404_16208_gb300 import ranc as mod
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ranc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ranc_create", "ranc_load_inputs", "ranc_step", "ranc_read_outputs", "ranc_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(ranc):
+    lib = C.CDLL(ranc.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(ranc.EXPORTED) == declared_functions()
+
+
+def test_struct_layout_matches_c(tmp_path, ranc):
+    exe = tmp_path / "abi_probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_probe.c"),
+                    "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    assert int(got["sizeof_dest"]) == C.sizeof(ranc.ranc_dest) == W.DEST_DTYPE.itemsize == 8
+    assert int(got["sizeof_desc"]) == C.sizeof(ranc.ranc_desc)
+    assert int(got["dest.delay"]) == ranc.ranc_dest.delay.offset
+    for f, _ in ranc.ranc_desc._fields_:
+        if f in got:
+            assert int(got[f]) == getattr(ranc.ranc_desc, f).offset, f
+
+
+def _expect_einval(ranc, net, batch=1, path=0, frag=""):
+    with pytest.raises(ranc.RancError) as ei:
+        ranc.ranc_create(net, batch, path)
+    assert ei.value.code == ranc.RANC_EINVAL, str(ei.value)
+    assert frag in str(ei.value)
+
+
+def small_net(**kw):
+    return W.random_net(5, 2, 1, axons=32, neurons=32, **kw)
+
+
+def test_rejects_delay_zero_and_sixteen(ranc):
+    for d in (0, 16):
+        net = small_net()
+        i = np.flatnonzero(net.dest["kind"].ravel() == W.KIND_CORE)[0]
+        net.dest.ravel()[i]["delay"] = d
+        _expect_einval(ranc, net, frag="delay")
+
+
+def test_rejects_axon_out_of_range(ranc):
+    net = small_net()
+    i = np.flatnonzero(net.dest["kind"].ravel() == W.KIND_CORE)[0]
+    net.dest.ravel()[i]["axon"] = 32
+    _expect_einval(ranc, net, frag="axon")
+
+
+def test_rejects_destination_that_is_not_a_core(ranc):
+    net = W.random_net(6, 2, 2, axons=32, neurons=32, holes=((1, 1),))
+    i = np.flatnonzero(net.dest["kind"].ravel() == W.KIND_CORE)[0]
+    c = i // 32
+    x, y = net.core_xy[c]
+    net.dest.ravel()[i]["dx"] = 1 - x
+    net.dest.ravel()[i]["dy"] = 1 - y
+    _expect_einval(ranc, net, frag="not a core")
+
+
+def test_rejects_output_id_and_weight_range_and_shapes(ranc):
+    net = small_net(p_out=0.5)
+    i = np.flatnonzero(net.dest["kind"].ravel() == W.KIND_OUTPUT)[0]
+    net.dest.ravel()[i]["axon"] = net.n_outputs
+    _expect_einval(ranc, net, frag="output id")
+    net = small_net()
+    net.weight[0, 0, 0] = 8  # weight_bits 4 allows +-7
+    _expect_einval(ranc, net, frag="weight")
+    _expect_einval(ranc, small_net(), batch=0, frag="batch")
+    _expect_einval(ranc, small_net(), path=7, frag="path")
+    net = small_net()
+    net.axon_type[0, 0] = net.n_types
+    _expect_einval(ranc, net, frag="axon_type")
+
+
+def test_rejects_possible_int32_overflow(ranc):
+    net = small_net()
+    net.pos_thr[0, 0] = 2**31 - 1
+    _expect_einval(ranc, net, frag="int32")
+
+
+def test_rejects_shared_grid_cell(ranc):
+    net = small_net()
+    net.core_xy[1] = net.core_xy[0]
+    _expect_einval(ranc, net, frag="share")
+
+
+def test_create_error_message_is_kept(ranc):
+    net = small_net()
+    net.axon_type[0, 0] = 99
+    with pytest.raises(ranc.RancError):
+        ranc.ranc_create(net, 1)
+    assert "axon_type" in ranc.ranc_last_error(None)
