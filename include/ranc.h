@@ -152,6 +152,11 @@ int ranc_read_outputs_device(ranc_sim *sim, uint32_t *counts);
  * (order independent, so it is computed on the device).  Synchronous. */
 int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint64_t *digest);
 
+/* Host copies for samples [b0, b0 + nb) only: v [nb][C][N], spikes
+ * [nb][C][N/32], same meaning as in ranc_read_state; either may be NULL.
+ * RANC_EINVAL when the range leaves the batch.  Synchronous. */
+int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes);
+
 /* counters[RANC_N_COUNTERS] summed over the batch since the last ranc_reset
  * (ranc_run_samples keeps accumulating across its windows).  Synchronous. */
 int ranc_read_counters(ranc_sim *sim, uint64_t *counters);

@@ -326,7 +326,7 @@ int canon_view(ranc_sim *sim, Canon &cv, bool need_ring) {
         dmalloc(&cv.spk, (size_t)sim->B * sim->C * (sim->N / 32)) != cudaSuccess ||
         (need_ring && dmalloc(&cv.ring, ring_words(sim)) != cudaSuccess))
         return fail(sim, RANC_ENOMEM, "temporary state buffers");
-    cudaError_t e = launch_batched_export(sim, cv.V, cv.spk, need_ring ? cv.ring : nullptr);
+    cudaError_t e = launch_batched_export(sim, 0, sim->B, cv.V, cv.spk, need_ring ? cv.ring : nullptr);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state export: %s", cudaGetErrorString(e));
     return RANC_OK;
 }
@@ -527,6 +527,32 @@ extern "C" int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint
     return sync_and_check(sim);
 }
 
+extern "C" int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes) {
+    CHECK_LIVE(sim);
+    if (b0 < 0 || nb < 0 || (long long)b0 + nb > sim->B) return fail(sim, RANC_EINVAL, "sample range outside the batch");
+    if (nb == 0) return RANC_OK;
+    const size_t per_v = (size_t)sim->C * sim->N, per_s = (size_t)sim->C * (sim->N / 32);
+    if (sim->path == RANC_PATH_PLAIN) {
+        if (v)
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, (int *)sim->V + (size_t)b0 * per_v, (size_t)nb * per_v * 4,
+                                              cudaMemcpyDeviceToHost, sim->stream));
+        if (spikes)
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, sim->spk + (size_t)b0 * per_s, (size_t)nb * per_s * 4,
+                                              cudaMemcpyDeviceToHost, sim->stream));
+        return sync_and_check(sim);
+    }
+    Canon cv;
+    cv.owned = true;
+    if (dmalloc(&cv.V, (size_t)nb * per_v) != cudaSuccess || dmalloc(&cv.spk, (size_t)nb * per_s) != cudaSuccess)
+        return fail(sim, RANC_ENOMEM, "temporary state buffers");
+    cudaError_t e = launch_batched_export(sim, b0, nb, cv.V, cv.spk, nullptr);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state export: %s", cudaGetErrorString(e));
+    if (v) CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, cv.V, (size_t)nb * per_v * 4, cudaMemcpyDeviceToHost, sim->stream));
+    if (spikes)
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, cv.spk, (size_t)nb * per_s * 4, cudaMemcpyDeviceToHost, sim->stream));
+    return sync_and_check(sim);
+}
+
 extern "C" int ranc_read_counters(ranc_sim *sim, uint64_t *counters) {
     CHECK_LIVE(sim);
     if (!counters) return fail(sim, RANC_EINVAL, "counters is NULL");
@@ -664,8 +690,8 @@ extern "C" int ranc_load_state(ranc_sim *sim, const void *buf, size_t n) {
             return fail(sim, RANC_ENOMEM, "temporary state buffers");
         CUDA_OR_FAIL(sim, cudaMemcpyAsync(cv.V, p, nv, cudaMemcpyHostToDevice, sim->stream));
         CUDA_OR_FAIL(sim, cudaMemcpyAsync(cv.ring, p + nv, nr, cudaMemcpyHostToDevice, sim->stream));
-        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->spk, p + nv + nr + no, ns, cudaMemcpyHostToDevice, sim->stream));
-        cudaError_t e = launch_batched_import(sim, cv.V, cv.ring);
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(cv.spk, p + nv + nr + no, ns, cudaMemcpyHostToDevice, sim->stream));
+        cudaError_t e = launch_batched_import(sim, cv.V, cv.spk, cv.ring);
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state import: %s", cudaGetErrorString(e));
         CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
     }

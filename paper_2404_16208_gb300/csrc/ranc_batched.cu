@@ -1,15 +1,781 @@
-// Batched path (placeholder until the tensor-core kernel lands).
+// Batched path: 128 samples per tile, crossbar integration on the
+// 5th-generation tensor cores (tcgen05), one persistent launch per tick.
+//
+// Per (core c, sample tile j) work item, one tick of Alg. 1:
+//   dV[n][m] = sum_a W[n][a] * S[m][a]            (Sec. II, Alg. 1 neuron block)
+// where S[m][a] in {0, 1} is "axon a of sample m is active" and
+// W[n][a] = w[type(a)][n] if axon a connects to neuron n, else 0 (the weight
+// chosen by axon type, folded into the connection matrix once at create).
+// Both operands are exact in fp16 (|w| <= 2047) and every partial sum is an
+// integer below 2^22 in magnitude, so fp32 accumulation in tensor memory is
+// exact and the result equals the integer sum of the CPU definition.
+//
+// Roles inside one CTA (416 threads, one CTA per SM, persistent over items):
+//   warps 0-7   epilogue: tensor memory -> registers (tcgen05.ld), potential
+//               update (leak, thresholds, reset), spike masks over 32 samples
+//               per neuron, delivery with one atomicOr per (neuron, 32 samples)
+//               into the sample-minor scheduler rows, output-bus counts;
+//   warps 8-11  producers: read and clear the scheduler row of tick t, OR the
+//               input lines of tick t, transpose 32x32 bit blocks and expand
+//               bits to fp16 0/1 operand tiles in the 128-byte swizzled
+//               K-major layout the tensor core reads;
+//   warp 12     tensor-memory allocation, TMA loads of the folded weights of
+//               the current core (cp.async.bulk.tensor, 128-byte swizzle),
+//               tcgen05.mma issue and commit.
+// Every mbarrier wait is bounded (global timer); a timeout sets the device
+// error word and all roles leave their loops, drain the tensor core and free
+// tensor memory before the CTA exits.
+//
+// Layouts (T tiles of 128 samples; sample m of tile j is batch index 128j+m):
+//   V     [T][C][4][N][32]   potentials (int16 when the range allows, else int32)
+//   ring  [T][C][16][A][4]   scheduler rows: word k of axon a holds samples 32k..32k+31
+//   spk   [T][C][4][N]       spike masks of the last tick (32 samples per word)
+//   inT   [T][ticks][Lpad][4] input lines, same sample-minor packing
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "ranc_internal.cuh"
+#include "ranc_ptx.cuh"
 
 namespace ranc {
-cudaError_t batched_setup(ranc_sim *, const ranc_desc *, std::string &why) {
-    why = "the batched path is not built in this version";
-    return cudaErrorInvalidValue;
+namespace {
+
+constexpr int kThreads = 416;
+constexpr int kEpiWarps = 8;
+constexpr int kProdWarp0 = 8;
+constexpr int kMmaWarp = 12;
+constexpr uint32_t kBlockBytes = 128u * 128u;  // 128 rows x 64 fp16 = one swizzled K-block
+
+struct TickArgs {
+    int C, A, N, NH, KB, T, n_valid, Lpad, in_ticks, n_out, neg_mode, items;
+    long long tick;
+    const int4 *prm;
+    const uint2 *dst;
+    const int *fin_ptr, *fin_line;
+    const uint16_t *outdeg;
+    const uint4 *inT;
+    void *V;
+    uint4 *ring;
+    uint32_t *spk, *out;
+    unsigned long long *cnt;
+    int *err;
+    uint32_t tmem_cols;
+};
+
+// ---------------------------------------------------------------------------
+// tcgen05 / TMA wrappers (inline PTX)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
-cudaError_t launch_batched_tick(ranc_sim *, const BatchedArgs &) { return cudaErrorNotSupported; }
-cudaError_t launch_batched_reset(ranc_sim *, bool) { return cudaErrorNotSupported; }
-cudaError_t launch_batched_inputs(ranc_sim *, const uint32_t *, int, int) { return cudaErrorNotSupported; }
-cudaError_t launch_batched_export(ranc_sim *, int *, uint32_t *, uint32_t *) { return cudaErrorNotSupported; }
-cudaError_t launch_batched_import(ranc_sim *, const int *, const uint32_t *) { return cudaErrorNotSupported; }
-void batched_teardown(ranc_sim *) {}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1u << 16;             // leading byte offset (unused for this swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1u << 46;             // version
+    d |= (uint64_t)2u << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D fp32, A and B fp16, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// 32 x 32 bit-matrix transpose across a warp: on return lane j holds the word
+// whose bit i is bit j of lane i's input word.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu : s == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y & ~m) >> s)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint32_t valid_mask(int n_valid, int first) {
+    const int k = n_valid - first;
+    return k >= 32 ? 0xffffffffu : (k <= 0 ? 0u : ((1u << k) - 1u));
+}
+
+// Integer value of an fp32 that holds an integer of magnitude < 2^22
+// (adding 1.5 * 2^23 puts it in the low mantissa bits).
+__device__ __forceinline__ int f32_to_int_exact(uint32_t bits) {
+    return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+template <typename VT>
+__device__ __forceinline__ void load32(const VT *p, int (&v)[32]) {
+    if constexpr (sizeof(VT) == 2) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(p);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint4 u = q[k];
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v[8 * k + 2 * e] = (int)(int16_t)(w[e] & 0xFFFFu);
+                v[8 * k + 2 * e + 1] = (int)w[e] >> 16;
+            }
+        }
+    } else {
+        const int4 *q = reinterpret_cast<const int4 *>(p);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int4 u = q[k];
+            v[4 * k] = u.x;
+            v[4 * k + 1] = u.y;
+            v[4 * k + 2] = u.z;
+            v[4 * k + 3] = u.w;
+        }
+    }
+}
+
+template <typename VT>
+__device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
+    if constexpr (sizeof(VT) == 2) {
+        uint4 *q = reinterpret_cast<uint4 *>(p);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                w[e] = ((uint32_t)v[8 * k + 2 * e] & 0xFFFFu) | ((uint32_t)v[8 * k + 2 * e + 1] << 16);
+            q[k] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        int4 *q = reinterpret_cast<int4 *>(p);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tick kernel
+// ---------------------------------------------------------------------------
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArgs a, const __grid_constant__ CUtensorMap wmap) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full[4], s_empty[4], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int NH = a.NH, KB = a.KB, C = a.C, A = a.A, N = a.N, T = a.T;
+    uint8_t *Wsm = base;                                   // [NH][KB] blocks of 128 rows x 128 B
+    uint8_t *Ssm = Wsm + (size_t)NH * KB * kBlockBytes;    // [KB] blocks
+    uint4 *lut = reinterpret_cast<uint4 *>(Ssm + (size_t)KB * kBlockBytes);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = (int)((long long)blockIdx.x * a.items / gridDim.x);
+    const int i1 = (int)((long long)(blockIdx.x + 1) * a.items / gridDim.x);
+    const int r0 = (int)(a.tick & (kRows - 1));
+
+    // 8 fp16 values (1.0 or 0.0) for every byte of spike bits.
+    for (int e = tid; e < 256; e += kThreads) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            w[q] = (((e >> (2 * q)) & 1) ? 0x3C00u : 0u) | (((e >> (2 * q + 1)) & 1) ? 0x3C000000u : 0u);
+        lut[e] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    if (tid == 0) {
+        mbar_init(&bar_w, 1);
+        mbar_init(&bar_drain, 1);
+        for (int k = 0; k < 4; ++k) {
+            mbar_init(&s_full[k], 2);
+            mbar_init(&s_empty[k], 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&acc_full[k], 1);
+            mbar_init(&acc_empty[k], kEpiWarps);
+        }
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    if (warp == kMmaWarp) tmem_alloc(&tmem_base_sh, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (abort_sh) return false;
+        if (mbar_wait_bounded(bar, parity)) return true;
+        abort_sh = 1;
+        atomicExch(a.err, kErrTimeout);
+        return false;
+    };
+
+    if (warp < kEpiWarps) {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3, g = warp >> 2;
+        VT *Vg = reinterpret_cast<VT *>(a.V);
+        for (int it = i0; it < i1; ++it) {
+            const int li = it - i0, c = it / T, j = it % T, buf = li & 1;
+            if (!wait(&acc_full[buf], (li >> 1) & 1)) break;
+            tc_fence_after();
+            uint32_t n_sp = 0, n_pk = 0, n_out = 0;
+            for (int k = 0; k < 2 * NH; ++k) {
+                __syncwarp();
+                const int u = g * 2 * NH + k, h = u >> 2, cc = u & 3;
+                const int n = h * 128 + q * 32 + lane;
+                const size_t cn = (size_t)c * N + n;
+                const int4 pr = a.prm[cn];  // leak, pos_thr, neg_thr, reset
+                const size_t vbase = ((((size_t)j * C + c) * 4 + cc) * N + n) * 32;
+                int v[32];
+                load32<VT>(Vg + vbase, v);
+                uint32_t d[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NH * 128 + h * 128 + cc * 32), d);
+                uint32_t mask = 0u;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int x = v[i] + f32_to_int_exact(d[i]) + pr.x;
+                    const bool fire = x >= pr.y;
+                    int y = a.neg_mode ? (x < pr.z ? pr.w : x) : max(x, pr.z);
+                    y = fire ? pr.w : y;
+                    v[i] = y;
+                    mask |= (fire ? 1u : 0u) << i;
+                }
+                store32<VT>(Vg + vbase, v);
+                a.spk[(((size_t)j * C + c) * 4 + cc) * N + n] = mask;
+                const uint32_t valid = valid_mask(a.n_valid, j * 128 + cc * 32);
+                const uint32_t live = mask & valid;
+                n_sp += __popc(live);
+                if (mask) {
+                    const uint2 dd = a.dst[cn];
+                    const uint32_t kind = dest_kind(dd);
+                    if (kind == RANC_DEST_CORE) {
+                        const uint32_t ax = dest_axon(dd);
+                        const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
+                        atomicOr(reinterpret_cast<uint32_t *>(a.ring) +
+                                     ((((size_t)j * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
+                                 mask);
+                        n_pk += __popc(live);
+                    } else if (kind == RANC_DEST_OUTPUT) {
+                        for (uint32_t m = live; m; m &= m - 1u) {
+                            const int b = j * 128 + cc * 32 + __ffs(m) - 1;
+                            atomicAdd(a.out + (size_t)b * a.n_out + dd.x, 1u);
+                        }
+                        n_out += __popc(live);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            n_sp = __reduce_add_sync(0xffffffffu, n_sp);
+            n_pk = __reduce_add_sync(0xffffffffu, n_pk);
+            n_out = __reduce_add_sync(0xffffffffu, n_out);
+            if (lane == 0 && (n_sp | n_pk | n_out)) {
+                unsigned long long *cp = a.cnt + ((size_t)j * C + c) * 4;
+                atomicAdd(cp + 0, (unsigned long long)n_sp);
+                atomicAdd(cp + 1, (unsigned long long)n_pk);
+                atomicAdd(cp + 2, (unsigned long long)n_out);
+            }
+        }
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------ producers
+        const int p = warp - kProdWarp0;
+        for (int it = i0; it < i1; ++it) {
+            const int li = it - i0, c = it / T, j = it % T;
+            bool ok = true;
+            unsigned long long ev = 0;
+            for (int kb = p >> 1; kb < KB; kb += 2) {
+                if (!wait(&s_empty[kb], (li & 1) ^ 1)) {
+                    ok = false;
+                    break;
+                }
+                const int ab = 2 * kb + (p & 1);
+                const int ax = 32 * ab + lane;
+                uint4 *rowp = a.ring + (((size_t)j * C + c) * kRows + r0) * A + ax;
+                uint4 R = *rowp;
+                *rowp = make_uint4(0u, 0u, 0u, 0u);
+                if (a.tick < a.in_ticks) {
+                    const int *fp = a.fin_ptr + (size_t)c * (A + 1) + ax;
+                    for (int k = fp[0]; k < fp[1]; ++k) {
+                        const uint4 I = a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + a.fin_line[k]];
+                        R.x |= I.x;
+                        R.y |= I.y;
+                        R.z |= I.z;
+                        R.w |= I.w;
+                    }
+                }
+                const uint32_t od = a.outdeg[(size_t)c * A + ax];
+                ev += (unsigned long long)od * (__popc(R.x & valid_mask(a.n_valid, j * 128)) +
+                                                __popc(R.y & valid_mask(a.n_valid, j * 128 + 32)) +
+                                                __popc(R.z & valid_mask(a.n_valid, j * 128 + 64)) +
+                                                __popc(R.w & valid_mask(a.n_valid, j * 128 + 96)));
+                uint8_t *blk = Ssm + (size_t)kb * kBlockBytes;
+                const uint32_t words[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t y = transpose32(words[w], lane);
+                    const int row = 32 * w + lane;
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const int chunk = (ab & 1) * 4 + qq;
+                        *reinterpret_cast<uint4 *>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) = lut[(y >> (8 * qq)) & 0xFFu];
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_full[kb]);
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+            if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        int loaded = -1;
+        uint32_t nw = 0, nd = 0;
+        bool w_pending = false;
+        const size_t vtile = (size_t)4 * N * 32 * sizeof(VT);
+        for (int it = i0; it < i1; ++it) {
+            const int li = it - i0, c = it / T, buf = li & 1;
+            if (c != loaded) {
+                if (loaded >= 0) {  // every MMA reading the old weights has finished
+                    mma_commit(&bar_drain);
+                    if (!wait(&bar_drain, nd & 1)) break;
+                    ++nd;
+                }
+                mbar_arrive_expect_tx(&bar_w, (uint32_t)N * A * 2);
+                for (int h = 0; h < NH; ++h)
+                    for (int kb = 0; kb < KB; ++kb)
+                        tma_load_3d(Wsm + (size_t)(h * KB + kb) * kBlockBytes, &wmap, kb * 64, h * 128, c, &bar_w);
+                w_pending = true;
+                if (!wait(&bar_w, nw & 1)) break;
+                w_pending = false;
+                ++nw;
+                loaded = c;
+            }
+            if (it + 1 < i1) {
+                const int c1 = (it + 1) / T, j1 = (it + 1) % T;
+                prefetch_l2(reinterpret_cast<const uint8_t *>(a.V) + ((size_t)j1 * C + c1) * vtile, (uint32_t)vtile);
+            }
+            if (!wait(&acc_empty[buf], ((li >> 1) & 1) ^ 1)) break;
+            tc_fence_after();
+            bool ok = true;
+            for (int kb = 0; kb < KB; ++kb) {
+                if (!wait(&s_full[kb], li & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int h = 0; h < NH; ++h) {
+                    const uint32_t d = tmem + (uint32_t)(buf * NH * 128 + h * 128);
+                    const uint32_t wa = smem_u32(Wsm + (size_t)(h * KB + kb) * kBlockBytes);
+                    const uint32_t sb = smem_u32(Ssm + (size_t)kb * kBlockBytes);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_f16(d, smem_desc(wa + ks * 32), smem_desc(sb + ks * 32), (kb | ks) != 0);
+                }
+                mma_commit(&s_empty[kb]);
+            }
+            if (!ok) break;
+            mma_commit(&acc_full[buf]);
+        }
+        // Drain: all MMAs issued by this thread complete before tensor memory is freed.
+        mma_commit(&bar_drain);
+        mbar_wait_bounded(&bar_drain, nd & 1);
+        if (w_pending) mbar_wait_bounded(&bar_w, nw & 1);  // a weight load still in flight
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) tmem_dealloc(tmem, a.tmem_cols);
+}
+
+// ---------------------------------------------------------------------------
+// Helper kernels: reset, input transposition, state export / import
+// ---------------------------------------------------------------------------
+
+template <typename VT>
+__global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long total) {
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total; f += (long long)gridDim.x * blockDim.x) {
+        const long long e = f / 32;  // ((j*C + c)*4 + cc)*N + n
+        const int n = (int)(e % N);
+        const int c = (int)((e / N / 4) % C);
+        V[f] = (VT)v0[(size_t)c * N + n];
+    }
+}
+
+// x [n_samples][ticks][words] -> inT [T][ticks][Lpad][4] (sample-minor).
+__global__ void transpose_inputs(const uint32_t *x, int n_samples, int ticks, int words, int T, uint32_t *inT) {
+    const int lane = threadIdx.x & 31;
+    const long long task = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long n_tasks = (long long)T * ticks * words * 4;
+    if (task >= n_tasks) return;
+    const int w = (int)(task % 4);
+    const int lb = (int)((task / 4) % words);
+    const int t = (int)((task / 4 / words) % ticks);
+    const int j = (int)(task / 4 / words / ticks);
+    const int s = j * 128 + w * 32 + lane;
+    const uint32_t word = s < n_samples ? x[((size_t)s * ticks + t) * words + lb] : 0u;
+    const uint32_t y = transpose32(word, lane);
+    inT[((((size_t)j * ticks + t) * words * 32) + lb * 32 + lane) * 4 + w] = y;
+}
+
+// Canonical copies of samples [b0, b0 + nb): v [nb][C][N], spk [nb][C][N/32],
+// ring [nb][C][16][A/32] (ring may be NULL).
+template <typename VT>
+__global__ void export_state(const VT *Vb, const uint32_t *spkb, const uint32_t *ringb, int b0, int nb, int C, int N,
+                             int A, int *v, uint32_t *spk, uint32_t *ring) {
+    const long long nv = (long long)nb * C * N, ns = (long long)nb * C * (N / 32),
+                    nr = ring ? (long long)nb * C * kRows * (A / 32) : 0;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nv + ns + nr;
+         f += (long long)gridDim.x * blockDim.x) {
+        if (f < nv) {
+            const int n = (int)(f % N), c = (int)((f / N) % C), b = b0 + (int)(f / N / C);
+            const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
+            v[f] = (int)Vb[((((size_t)j * C + c) * 4 + cc) * N + n) * 32 + i];
+        } else if (f < nv + ns) {
+            const long long g = f - nv;
+            const int wn = (int)(g % (N / 32)), c = (int)((g / (N / 32)) % C), b = b0 + (int)(g / (N / 32) / C);
+            const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
+            uint32_t word = 0;
+            for (int k = 0; k < 32; ++k)
+                word |= ((spkb[(((size_t)j * C + c) * 4 + cc) * N + wn * 32 + k] >> i) & 1u) << k;
+            spk[g] = word;
+        } else {
+            const long long g = f - nv - ns;
+            const int AW = A / 32;
+            const int aw = (int)(g % AW), r = (int)((g / AW) % kRows), c = (int)((g / AW / kRows) % C),
+                      b = b0 + (int)(g / AW / kRows / C);
+            const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
+            uint32_t word = 0;
+            for (int k = 0; k < 32; ++k)
+                word |= ((ringb[((((size_t)j * C + c) * kRows + r) * A + aw * 32 + k) * 4 + cc] >> i) & 1u) << k;
+            ring[g] = word;
+        }
+    }
+}
+
+template <typename VT>
+__global__ void import_state(VT *Vb, uint32_t *spkb, uint32_t *ringb, int B, int T, int C, int N, int A, const int *v,
+                             const uint32_t *spk, const uint32_t *ring) {
+    const long long nv = (long long)B * C * N, ns = (long long)T * C * 4 * N, nr = (long long)T * C * kRows * A * 4;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nv + ns + nr;
+         f += (long long)gridDim.x * blockDim.x) {
+        if (f < nv) {
+            const int n = (int)(f % N), c = (int)((f / N) % C), b = (int)(f / N / C);
+            const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
+            Vb[((((size_t)j * C + c) * 4 + cc) * N + n) * 32 + i] = (VT)v[f];
+        } else if (f < nv + ns) {
+            const long long g = f - nv;  // ((j*C + c)*4 + cc)*N + n
+            const int n = (int)(g % N), cc = (int)((g / N) % 4), c = (int)((g / N / 4) % C), j = (int)(g / N / 4 / C);
+            uint32_t word = 0;
+            for (int i = 0; i < 32; ++i) {
+                const int b = j * 128 + cc * 32 + i;
+                if (b < B) word |= ((spk[((size_t)b * C + c) * (N / 32) + n / 32] >> (n & 31)) & 1u) << i;
+            }
+            spkb[g] = word;
+        } else {
+            const long long g = f - nv - ns;  // (((j*C + c)*16 + r)*A + a)*4 + cc
+            const int cc = (int)(g % 4), ax = (int)((g / 4) % A), r = (int)((g / 4 / A) % kRows),
+                      c = (int)((g / 4 / A / kRows) % C), j = (int)(g / 4 / A / kRows / C);
+            uint32_t word = 0;
+            for (int i = 0; i < 32; ++i) {
+                const int b = j * 128 + cc * 32 + i;
+                if (b < B)
+                    word |= ((ring[(((size_t)b * C + c) * kRows + r) * (A / 32) + ax / 32] >> (ax & 31)) & 1u) << i;
+            }
+            ringb[g] = word;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct Batched {
+    int NH = 0, KB = 0, Lpad = 0, n_sm = 0;
+    uint32_t tmem_cols = 0;
+    size_t smem = 0;
+    __half *wfold = nullptr;
+    int *fin_ptr = nullptr, *fin_line = nullptr;
+    uint16_t *outdeg = nullptr;
+    uint4 *inT = nullptr;
+    size_t inT_cap = 0;
+    CUtensorMap wmap;  // 64-byte aligned by its declaration
+};
+
+Batched *B_of(ranc_sim *s) { return static_cast<Batched *>(s->tmap); }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+long long grid_for(long long n) { return std::max<long long>(1, std::min<long long>((n + 255) / 256, 8192)); }
+
+}  // namespace
+
+cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
+    const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types;
+    if (!(N == 128 || N == 256) || A % 64 != 0 || A < 64 || A > 256) {
+        why = "the batched path needs neurons in {128, 256} and axons a multiple of 64 in [64, 256]";
+        return cudaErrorInvalidValue;
+    }
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, sim->device);
+    if (e != cudaSuccess) {
+        why = "cudaGetDeviceProperties";
+        return e;
+    }
+    if (prop.major != 10 || prop.minor != 3) {
+        why = "the batched path needs an sm_103 (GB300) device";
+        return cudaErrorInvalidValue;
+    }
+    Batched *bs = new (std::nothrow) Batched();
+    if (!bs) {
+        why = "host allocation";
+        return cudaErrorMemoryAllocation;
+    }
+    sim->tmap = bs;
+    bs->NH = N / 128;
+    bs->KB = A / 64;
+    bs->Lpad = sim->in_words * 32;
+    bs->n_sm = prop.multiProcessorCount;
+    bs->tmem_cols = bs->NH == 2 ? 512u : 256u;
+    bs->smem = (size_t)(bs->NH + 1) * bs->KB * kBlockBytes + 256 * 16 + 1024;
+    sim->T = (sim->B + kTileS - 1) / kTileS;
+    sim->B_pad = sim->T * kTileS;
+
+    // Potentials fit int16 when every value a neuron can hold does.
+    bool v16 = true;
+    for (size_t i = 0; i < (size_t)C * N; i++) {
+        const long long hi = std::max({(long long)d->pos_thr[i] - 1, (long long)d->reset[i], (long long)d->v0[i]});
+        const long long lo = std::min({(long long)d->neg_thr[i], (long long)d->reset[i], (long long)d->v0[i]});
+        if (hi > 32767 || lo < -32768) v16 = false;
+    }
+    sim->v16 = v16 ? 1 : 0;
+
+    // Folded weights W[c][n][a] = connected(a, n) ? w[type(a)][n] : 0 (fp16, exact).
+    std::vector<__half> wf((size_t)C * N * A);
+    std::vector<uint16_t> od((size_t)C * A, 0);
+    const int NWd = N / 32;
+    for (int c = 0; c < C; c++)
+        for (int ax = 0; ax < A; ax++) {
+            const uint32_t *row = d->crossbar + ((size_t)c * A + ax) * NWd;
+            const int k = d->axon_type[(size_t)c * A + ax];
+            for (int n = 0; n < N; n++) {
+                const bool on = (row[n >> 5] >> (n & 31)) & 1u;
+                wf[((size_t)c * N + n) * A + ax] = __float2half((float)(on ? d->weight[((size_t)c * K + k) * N + n] : 0));
+                od[(size_t)c * A + ax] += on ? 1 : 0;
+            }
+        }
+    // Input fan-in per (core, axon).
+    std::vector<int> fptr((size_t)C * (A + 1), 0), fline;
+    {
+        std::vector<std::vector<int>> lists((size_t)C * A);
+        const int nnz = d->n_inputs > 0 ? d->in_offsets[d->n_inputs] : 0;
+        (void)nnz;
+        for (int i = 0; i < d->n_inputs; i++)
+            for (int k = d->in_offsets[i]; k < d->in_offsets[i + 1]; k++)
+                lists[(size_t)d->in_core[k] * A + d->in_axon[k]].push_back(i);
+        for (int c = 0; c < C; c++) {
+            for (int ax = 0; ax < A; ax++) {
+                fptr[(size_t)c * (A + 1) + ax] = (int)fline.size();
+                for (int L : lists[(size_t)c * A + ax]) fline.push_back(L);
+            }
+            fptr[(size_t)c * (A + 1) + A] = (int)fline.size();
+        }
+        if (fline.empty()) fline.push_back(0);
+    }
+    const size_t vsz = v16 ? 2 : 4;
+    if (cudaMalloc(&bs->wfold, wf.size() * 2) != cudaSuccess || cudaMalloc(&bs->outdeg, od.size() * 2) != cudaSuccess ||
+        cudaMalloc(&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
+        cudaMalloc(&bs->fin_line, fline.size() * 4) != cudaSuccess ||
+        cudaMalloc(&sim->V, (size_t)sim->T * C * 4 * N * 32 * vsz) != cudaSuccess ||
+        cudaMalloc(&sim->ring, (size_t)sim->T * C * kRows * A * 16) != cudaSuccess ||
+        cudaMalloc(&sim->spk, (size_t)sim->T * C * 4 * N * 4) != cudaSuccess ||
+        cudaMalloc(&sim->out, (size_t)sim->B_pad * sim->n_outputs * 4) != cudaSuccess ||
+        cudaMalloc(&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess) {
+        why = "device allocation of the batched state failed";
+        return cudaErrorMemoryAllocation;
+    }
+    sim->cnt_len = (size_t)sim->T * C * 4;
+    if ((e = cudaMemcpy(bs->wfold, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->fin_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        why = "copy of the batched network arrays";
+        return e;
+    }
+
+    // Tensor map of the folded weights: dims (A, N, C), box (64, 128, 1), 128-byte swizzle.
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if ((e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q)) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        why = "cuTensorMapEncodeTiled is unavailable";
+        return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)A, (cuuint64_t)N, (cuuint64_t)C};
+    const cuuint64_t strides[2] = {(cuuint64_t)A * 2, (cuuint64_t)N * A * 2};
+    const cuuint32_t box[3] = {64, 128, 1}, estr[3] = {1, 1, 1};
+    CUresult cr = reinterpret_cast<EncodeTiledFn>(fn)(&bs->wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, bs->wfold, dims,
+                                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        why = "cuTensorMapEncodeTiled failed";
+        return cudaErrorInvalidValue;
+    }
+    e = v16 ? cudaFuncSetAttribute(batched_tick_kernel<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem)
+            : cudaFuncSetAttribute(batched_tick_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem);
+    if (e != cudaSuccess) why = "kernel shared-memory attribute";
+    return e;
+}
+
+cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
+    Batched *bs = B_of(sim);
+    TickArgs a{};
+    a.C = sim->C; a.A = sim->A; a.N = sim->N; a.NH = bs->NH; a.KB = bs->KB; a.T = sim->T;
+    a.n_valid = sim->n_valid; a.Lpad = bs->Lpad; a.in_ticks = bs->inT ? sim->in_ticks : 0; a.n_out = sim->n_outputs;
+    a.neg_mode = sim->neg_mode; a.items = sim->T * sim->C; a.tick = sim->tick;
+    a.prm = sim->prm; a.dst = sim->dst; a.fin_ptr = bs->fin_ptr; a.fin_line = bs->fin_line; a.outdeg = bs->outdeg;
+    a.inT = bs->inT; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
+    a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
+    const int grid = std::min(bs->n_sm, a.items);
+    if (sim->v16)
+        batched_tick_kernel<int16_t><<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
+    else
+        batched_tick_kernel<int><<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
+    const long long total = (long long)sim->T * sim->C * 4 * sim->N * 32;
+    if (sim->v16)
+        batched_reset_v<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int16_t *)sim->V, sim->v0, sim->C, sim->N, total);
+    else
+        batched_reset_v<int><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int *)sim->V, sim->v0, sim->C, sim->N, total);
+    sim->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sim->ring, 0, (size_t)sim->T * sim->C * kRows * sim->A * 16, sim->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sim->spk, 0, (size_t)sim->T * sim->C * 4 * sim->N * 4, sim->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B_pad * sim->n_outputs * 4, sim->stream)) != cudaSuccess) return e;
+    if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks) {
+    Batched *bs = B_of(sim);
+    const size_t need = (size_t)sim->T * n_ticks * bs->Lpad;  // uint4 units
+    if (need > bs->inT_cap) {
+        cudaError_t e = cudaStreamSynchronize(sim->stream);
+        if (e != cudaSuccess) return e;
+        if (bs->inT) cudaFree(bs->inT);
+        bs->inT = nullptr;
+        bs->inT_cap = 0;
+        if (cudaMalloc(&bs->inT, need * 16) != cudaSuccess) return cudaErrorMemoryAllocation;
+        bs->inT_cap = need;
+    }
+    const long long threads = (long long)sim->T * n_ticks * sim->in_words * 4 * 32;
+    transpose_inputs<<<(unsigned)((threads + 255) / 256), 256, 0, sim->stream>>>(dev_bits, n_samples, n_ticks,
+                                                                                sim->in_words, sim->T, (uint32_t *)bs->inT);
+    sim->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk, uint32_t *ring) {
+    const long long total = (long long)nb * sim->C * sim->N + (long long)nb * sim->C * (sim->N / 32) +
+                            (ring ? (long long)nb * sim->C * kRows * (sim->A / 32) : 0);
+    if (sim->v16)
+        export_state<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (const int16_t *)sim->V, sim->spk, sim->ring, b0, nb, sim->C, sim->N, sim->A, v, spk, ring);
+    else
+        export_state<int><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (const int *)sim->V, sim->spk, sim->ring, b0, nb, sim->C, sim->N, sim->A, v, spk, ring);
+    sim->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *spk, const uint32_t *ring) {
+    const long long total = (long long)sim->B * sim->C * sim->N + (long long)sim->T * sim->C * 4 * sim->N +
+                            (long long)sim->T * sim->C * kRows * sim->A * 4;
+    if (sim->v16)
+        import_state<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (int16_t *)sim->V, sim->spk, sim->ring, sim->B, sim->T, sim->C, sim->N, sim->A, v, spk, ring);
+    else
+        import_state<int><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (int *)sim->V, sim->spk, sim->ring, sim->B, sim->T, sim->C, sim->N, sim->A, v, spk, ring);
+    sim->launches++;
+    return cudaGetLastError();
+}
+
+void batched_teardown(ranc_sim *sim) {
+    Batched *bs = B_of(sim);
+    if (!bs) return;
+    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete bs;
+    sim->tmap = nullptr;
+}
+
 }  // namespace ranc

@@ -85,7 +85,7 @@ struct ranc_sim {
     int *in_ptr = nullptr, *in_line = nullptr, *in_axon = nullptr;
     int *v0 = nullptr;
     void *wfold = nullptr;              // batched: [C][N][A] fp16 folded weights
-    void *tmap = nullptr;               // batched: CUtensorMap storage (host)
+    void *tmap = nullptr;               // batched: path-specific host state (tensor map, tables)
 
     // state (device)
     void *V = nullptr;
@@ -128,7 +128,9 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
 cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
-cudaError_t launch_batched_export(ranc_sim *sim, int *v_canon, uint32_t *spk_canon, uint32_t *ring_canon);
-cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *ring_canon);
+cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, uint32_t *spk_canon,
+                                  uint32_t *ring_canon);
+cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *spk_canon,
+                                  const uint32_t *ring_canon);
 void batched_teardown(ranc_sim *sim);
 }  // namespace ranc

@@ -20,7 +20,7 @@ RANC_PATH_PLAIN, RANC_PATH_BATCHED = 0, 1
 RANC_MEM_HOST, RANC_MEM_DEVICE = 0, 1
 COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
 EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
-            "ranc_read_outputs_device", "ranc_read_state", "ranc_read_counters", "ranc_get_tick", "ranc_reset",
+            "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
             "ranc_read_kernel_timing", "ranc_launch_count", "ranc_destroy", "ranc_last_error")
 
@@ -58,6 +58,7 @@ def load_library(path=LIB_PATH):
         "ranc_read_outputs": ([vp, u32p], C.c_int),
         "ranc_read_outputs_device": ([vp, vp], C.c_int),
         "ranc_read_state": ([vp, vp, vp, u64p], C.c_int),
+        "ranc_read_sample_state": ([vp, i32, i32, vp, vp], C.c_int),
         "ranc_read_counters": ([vp, u64p], C.c_int),
         "ranc_get_tick": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_reset": ([vp], C.c_int),
@@ -140,6 +141,13 @@ def ranc_read_state(h, batch, n_cores, neurons, want_v=True, want_spikes=True, w
     _check(_lib.ranc_read_state(h, _p(v) if want_v else None, _p(s) if want_spikes else None,
                                 _p(d) if want_digest else None), h)
     return v, s, (int(d[0]) if want_digest else None)
+
+
+def ranc_read_sample_state(h, b0, nb, n_cores, neurons):
+    v = np.zeros((nb, n_cores, neurons), np.int32)
+    s = np.zeros((nb, n_cores, neurons // 32), np.uint32)
+    _check(_lib.ranc_read_sample_state(h, int(b0), int(nb), _p(v), _p(s)), h)
+    return v, s
 
 
 def ranc_read_counters(h):
@@ -225,6 +233,9 @@ class Sim:
 
     def state(self, **kw):
         return ranc_read_state(self.h, self.batch, self.net.n_cores, self.net.neurons, **kw)
+
+    def sample_state(self, b0, nb):
+        return ranc_read_sample_state(self.h, b0, nb, self.net.n_cores, self.net.neurons)
 
     def counters(self):
         return ranc_read_counters(self.h)

@@ -1,0 +1,165 @@
+"""Batched tensor-core path against the CPU oracle, bit for bit: potentials,
+spikes and output counts per tick on small networks and ragged batches, and
+sampled samples of the 4096-sample, 512-core configuration that the benchmark
+times (same handle shape and launch configuration)."""
+
+import os
+
+import numpy as np
+import pytest
+
+import ranc_workloads as W
+from parity_util import digest, gpu_trace, unpack_spikes
+
+pytestmark = pytest.mark.gpu
+NPROC = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def ranc():
+    from paper_2404_16208_gb300 import build_library
+    build_library()
+    from paper_2404_16208_gb300 import ranc as mod
+    return mod
+
+
+def per_tick_parity(ranc, oracle_mod, net, x, T):
+    B = x.shape[0]
+    ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
+    sim = ranc.Sim(net, B, ranc.RANC_PATH_BATCHED)
+    sim.load_inputs(x)
+    v, s, d = gpu_trace(sim, T)
+    for t in range(T):
+        np.testing.assert_array_equal(v[:, t], ref["v_trace"][:, t], err_msg=f"tick {t}")
+        np.testing.assert_array_equal(s[:, t], ref["spike_trace"][:, t], err_msg=f"tick {t}")
+        assert d[t] == digest(ref["v_trace"][:, t]), t
+    np.testing.assert_array_equal(sim.outputs(), ref["out"])
+    cnt = sim.counters()
+    np.testing.assert_array_equal(cnt[:4], ref["counters"][:, :4].sum(0))
+    assert cnt[4] == B * T
+    sim.close()
+    return ref
+
+
+def test_tiny_workload_one_padded_tile(ranc, oracle_mod):
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(net.meta["seed"], 64, 8, 784, 0.15)
+    per_tick_parity(ranc, oracle_mod, net, x, 9)
+
+
+SHAPES = [
+    # grid, axons, neurons, types, neg_mode, delay_max, batch, v0, weight limit / bits
+    ((2, 2), 64, 128, 2, 0, 15, 128, (0, 0), (7, 4)),
+    ((3, 1), 128, 256, 4, 1, 5, 130, (-3, 3), (255, 9)),
+    ((2, 2), 192, 128, 8, 0, 9, 257, (-5, 5), (2047, 12)),
+    ((1, 3), 256, 256, 3, 1, 15, 40, (0, 4), (100, 8)),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{s[1]}x{s[2]}b{s[6]}" for s in SHAPES])
+def test_random_nets_every_tick(ranc, oracle_mod, shape):
+    (gw, gh), A, N, K, neg, dmax, B, v0, (wl, wb) = shape
+    net = W.random_net(200 + A + N, gw, gh, axons=A, neurons=N, n_types=K, neg_mode=neg, delay_max=dmax,
+                       v0=v0, n_inputs=90, fanout_per_line=4, p_core=0.6, p_out=0.2, w_lim=wl,
+                       weight_bits=wb, pthr=(1, 3 * wl), nthr=(-3 * wl, -1), leak=(-2, 2))
+    x = W.rate_coded_inputs(9, B, 10, net.n_inputs, 0.3)
+    ref = per_tick_parity(ranc, oracle_mod, net, x, 18)
+    assert ref["counters"][:, 1].sum() > 0
+
+
+def test_int32_potentials_when_int16_cannot_hold_them(ranc, oracle_mod):
+    net = W.random_net(301, 2, 1, axons=64, neurons=128, w_lim=2047, weight_bits=12, pthr=(30000, 60000),
+                       nthr=(-60000, -30000), leak=(-5, 5), n_inputs=40, fanout_per_line=6)
+    x = W.rate_coded_inputs(10, 150, 8, net.n_inputs, 0.5)
+    per_tick_parity(ranc, oracle_mod, net, x, 12)
+
+
+SAMPLED = [0, 1, 127, 128, 1000, 2047, 2048, 3001, 4094, 4095]
+
+
+def test_mnist512_full_batch_sampled(ranc, oracle_mod):
+    """The benchmark's handle: 512 cores, 4096 samples in 32 tiles, 24 ticks.
+    Sampled samples are compared with the oracle in full (every potential and
+    spike of the last tick, output counts); the digest of every potential of
+    the sampled samples is compared after every tick."""
+    net = W.mnist_512core()
+    B = 4096
+    x = W.rate_coded_inputs(net.meta["seed"], B, 16, 784, 0.15)
+    xs = x[SAMPLED]
+    ref = oracle_mod.run(net, xs, 24, trace=True, n_threads=NPROC)
+    sim = ranc.Sim(net, B, ranc.RANC_PATH_BATCHED)
+    sim.load_inputs(x)
+    for t in range(24):
+        sim.step(1)
+        for k, b in enumerate(SAMPLED):
+            v, s = sim.sample_state(b, 1)
+            np.testing.assert_array_equal(v[0], ref["v_trace"][k, t], err_msg=f"sample {b} tick {t}")
+            np.testing.assert_array_equal(unpack_spikes(s[0], 256), ref["spike_trace"][k, t])
+    out = sim.outputs()
+    np.testing.assert_array_equal(out[SAMPLED], ref["out"])
+    cnt = sim.counters()
+    assert cnt[4] == B * 24
+    # every sample: output events and spikes are consistent with the counters
+    assert int(out.sum()) == int(cnt[2])
+    sim.close()
+
+
+def test_batched_equals_plain_on_every_sample_of_a_large_batch(ranc, oracle_mod):
+    """All 1000 samples (8 tiles, ragged) through both paths; the plain path
+    is pinned to the oracle separately, and both are compared with the oracle
+    on a sampled subset here."""
+    net = W.mnist_512core()
+    B = 1000
+    x = W.rate_coded_inputs(net.meta["seed"], B, 16, 784, 0.15, first_sample=5000)
+    res = {}
+    for path in (ranc.RANC_PATH_PLAIN, ranc.RANC_PATH_BATCHED):
+        sim = ranc.Sim(net, B, path)
+        sim.load_inputs(x)
+        sim.step(24)
+        res[path] = (sim.outputs(), sim.state()[2], sim.counters())
+        sim.close()
+    a, b = res[ranc.RANC_PATH_PLAIN], res[ranc.RANC_PATH_BATCHED]
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1]
+    np.testing.assert_array_equal(a[2], b[2])
+    sel = [0, 511, 999]
+    ref = oracle_mod.run(net, x[sel], 24, n_threads=NPROC)
+    np.testing.assert_array_equal(b[0][sel], ref["out"])
+
+
+def test_run_samples_ragged_groups_batched(ranc, oracle_mod):
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(4, 300, 8, 784, 0.15)
+    ref = oracle_mod.run(net, x, 9, n_threads=NPROC)
+    sim = ranc.Sim(net, 128, ranc.RANC_PATH_BATCHED)
+    np.testing.assert_array_equal(sim.run_samples(x, 9), ref["out"])
+    np.testing.assert_array_equal(sim.counters()[:4], ref["counters"][:, :4].sum(0))
+    sim.close()
+
+
+def test_checkpoint_round_trip_batched(ranc, oracle_mod):
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(12, 130, 8, 784, 0.2)
+    ref = oracle_mod.run(net, x, 12, n_threads=NPROC)
+    a = ranc.Sim(net, 130, ranc.RANC_PATH_BATCHED)
+    a.load_inputs(x)
+    a.step(4)
+    buf = a.save()
+    b = ranc.Sim(net, 130, ranc.RANC_PATH_BATCHED)
+    b.load_inputs(x)
+    b.load(buf)
+    for s in (a, b):
+        s.step(8)
+        np.testing.assert_array_equal(s.state()[0], ref["v"])
+        np.testing.assert_array_equal(s.outputs(), ref["out"])
+        np.testing.assert_array_equal(s.counters()[:4], ref["counters"][:, :4].sum(0))
+    # a plain-path checkpoint has the same canonical content but another path tag
+    a.close()
+    b.close()
+
+
+def test_batched_rejects_unsupported_shapes(ranc):
+    net = W.random_net(5, 2, 1, axons=32, neurons=32)
+    with pytest.raises(ranc.RancError) as ei:
+        ranc.ranc_create(net, 128, ranc.RANC_PATH_BATCHED)
+    assert ei.value.code == ranc.RANC_EINVAL
