@@ -173,6 +173,62 @@ def plain_bytes_per_core_tick(net):
             + N // 8)           # spike bitmap
 
 
+def batched_bytes_per_sample_core_tick(net, vbytes):
+    """Algorithmic bytes per (sample, core, tick) of the batched tick kernel:
+    the potential read and written once, the scheduler row read and cleared,
+    the spike mask recorded.  Weights and parameters are amortised over 4096
+    samples and left out."""
+    A, N = net.axons, net.neurons
+    return 2 * N * vbytes + 2 * A // 8 + N // 8
+
+
+def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
+    """Batched path: one handle of n_samples; a step is one sample window
+    (reset, input transposition, 24 ticks, output copy) on the device."""
+    sim = ranc.Sim(net, n_samples, ranc.RANC_PATH_BATCHED)
+    dout = torch.zeros((n_samples, net.n_outputs), dtype=torch.int32, device="cuda")
+    run = lambda: ranc.ranc_run_samples(sim.h, dx.data_ptr(), n_samples, T_IN, WINDOW, dout.data_ptr(),
+                                        ranc.RANC_MEM_DEVICE)
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    ranc.ranc_reset(sim.h)
+    l0 = ranc.ranc_launch_count(sim.h)
+    ms = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    launches = ranc.ranc_launch_count(sim.h) - l0
+    cnt = ranc.ranc_read_counters(sim.h)
+    ranc.ranc_set_kernel_timing(sim.h, True)
+    run()
+    kms, kn = ranc.ranc_read_kernel_timing(sim.h)
+    ranc.ranc_set_kernel_timing(sim.h, False)
+    counts = dout.cpu().numpy()
+    sim.close()
+    return dict(ms=ms, samples=n_samples * steps, events=int(cnt[3]), launches=launches, kernel_ms=kms,
+                kernel_launches=kn, counts=counts)
+
+
+def e2e_batched(ranc, torch, net, x, n_samples):
+    """The same step through the C ABI with host buffers (pinned): input bits
+    copied in and output counts copied out inside the timed region."""
+    xh = torch.from_numpy(x[:n_samples].copy()).pin_memory().numpy()
+    ch = torch.zeros((n_samples, net.n_outputs), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    sim = ranc.Sim(net, n_samples, ranc.RANC_PATH_BATCHED)
+    ranc.ranc_run_samples(sim.h, xh, n_samples, T_IN, WINDOW, ch)
+    reps, t0 = 3, time.perf_counter()
+    for _ in range(reps):
+        ranc.ranc_run_samples(sim.h, xh, n_samples, T_IN, WINDOW, ch)
+    dt = (time.perf_counter() - t0) / reps
+    sim.close()
+    return dict(value=n_samples / dt, h2d=int(xh.nbytes), d2h=int(ch.nbytes))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +236,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--plain-samples", type=int, default=PLAIN_SAMPLES)
+    ap.add_argument("--batch-samples", type=int, default=BATCH_SAMPLES,
+                    help="samples per batched step (profiling runs use a smaller case)")
+    ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, ws, local = dist_env()
@@ -225,62 +284,87 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     pk = peaks()
-    # Samples are independent: each rank takes its own slice (no data-path collective).
-    first = rank * args.plain_samples
-    net, x = make_workload(first, args.plain_samples)
+    # Samples are independent: each rank simulates its own slice of samples
+    # (no data-path collective); only the step time is reduced (max over ranks).
+    nb, npl = args.batch_samples, args.plain_samples
+    legs = set(args.legs.split(","))
+    net, x = make_workload(rank * max(nb, npl), max(nb, npl))
     dx = torch.from_numpy(x.view(np.int32)).cuda()
     flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def max_over_ranks(v):
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # Clocks are sampled over both legs (warm-up and timed steps).
     with Clocks(torch.cuda.current_device()) as clk:
-        pr = bench_plain(ranc, torch, net, dx, args.plain_samples, args.steps, args.warmup, flush)
-    t_plain = torch.tensor([pr["ms"]], device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_plain, op=dist.ReduceOp.MAX)
-    ms_plain = float(t_plain.item())
+        br = bench_batched(ranc, torch, net, dx[:nb], nb, args.steps, args.warmup)
+        ms_b = max_over_ranks(br["ms"])
+        if "plain" in legs:
+            if ws > 1:
+                dist.barrier()
+            pr = bench_plain(ranc, torch, net, dx[:npl], npl, max(1, min(args.steps, 2)), 1, flush)
+            ms_p = max_over_ranks(pr["ms"])
+    if "plain" not in legs:
+        samples = br["samples"] * ws
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": samples / (ms_b * 1e-3), "unit": "samples/s",
+                              "legs": "batched only (profiling case)", "samples_per_step": nb,
+                              "ms_per_step": ms_b / args.steps}))
+        return
 
-    # roofline of the dominant kernel (plain tick kernel for now)
-    kavg = pr["kernel_ms"] / max(pr["kernel_launches"], 1)
-    bytes_launch = plain_bytes_per_core_tick(net) * net.n_cores
-    achieved = bytes_launch / (kavg * 1e-3) / 1e9
-    roof = {"kernel": "plain_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+    # Roofline of the dominant kernel (the batched tick kernel).
+    vbytes = 2  # int16 potentials: this workload's range [-1024, 2047] fits
+    kavg_ms = br["kernel_ms"] / max(br["kernel_launches"], 1)
+    units = nb * net.n_cores
+    bytes_launch = batched_bytes_per_sample_core_tick(net, vbytes) * units
+    achieved = bytes_launch / (kavg_ms * 1e-3) / 1e9
+    flops_launch = 2.0 * net.axons * net.neurons * (-(-nb // 128) * 128) * net.n_cores
+    tflops = flops_launch / (kavg_ms * 1e-3) / 1e12
+    roof = {"kernel": "batched_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-            "peak_source": pk["source"], "avg_launch_us": kavg * 1e3, "bytes_per_launch": bytes_launch}
-
-    # e2e: host buffers through the C ABI (plain leg until the batched path lands)
-    e2e_n = min(args.plain_samples, 2000)
-    xh = torch.from_numpy(x[:e2e_n].copy()).pin_memory().numpy()
-    ch = torch.zeros((e2e_n, net.n_outputs), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
-    sim = ranc.Sim(net, 1, ranc.RANC_PATH_PLAIN)
-    ranc.ranc_run_samples(sim.h, xh, e2e_n, T_IN, WINDOW, ch)
-    t0 = time.perf_counter()
-    ranc.ranc_run_samples(sim.h, xh, e2e_n, T_IN, WINDOW, ch)
-    e2e_s = time.perf_counter() - t0
-    sim.close()
+            "peak_source": pk["source"] + " (hbm_gbs, of measured copy bandwidth)",
+            "avg_launch_us": kavg_ms * 1e3, "bytes_per_launch": bytes_launch,
+            "tensor": {"achieved_tflops": tflops, "peak_tflops": pk["bf16_tflops_sustained"],
+                       "frac": tflops / pk["bf16_tflops_sustained"], "kind": "tcgen05.mma kind::f16 (fp16, fp32 accumulate)"}}
+    ekp = pr["kernel_ms"] / max(pr["kernel_launches"], 1)
+    pbytes = plain_bytes_per_core_tick(net) * net.n_cores
+    plain = {"samples_per_sec": pr["samples"] * ws / (ms_p * 1e-3),
+             "synaptic_events_per_sec": pr["events"] * ws / (ms_p * 1e-3),
+             "ms_per_step": ms_p / max(1, min(args.steps, 2)), "samples_per_step": npl, "batch": 1,
+             "kernel": {"name": "plain_tick_kernel", "avg_launch_us": ekp * 1e3,
+                        "achieved_gbs": pbytes / (ekp * 1e-3) / 1e9,
+                        "frac_hbm": pbytes / (ekp * 1e-3) / 1e9 / pk["hbm_gbs"]}}
+    e2e = e2e_batched(ranc, torch, net, x, nb)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cr = oracle_rate(net, x[:256])
         cpu = {"value": cr["samples_per_s"], "unit": "samples/s", "cores": cr["threads"], "kind": "oracle",
-               "sample": f"{cr['samples']} samples of the 512-core workload ({cr['seconds']:.1f} s)",
+               "sample": f"{cr['samples']} samples of the 512-core workload, 24 ticks each ({cr['seconds']:.1f} s)",
                "synaptic_events_per_sec": cr["events_per_s"]}
 
-    samples_total = pr["samples"] * ws
-    val = samples_total / (ms_plain * 1e-3)
+    samples_total = br["samples"] * ws
     line = {
-        "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_plain / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "synaptic_events_per_sec": pr["events"] * ws / (ms_plain * 1e-3),
-        "config": {"workload": f"mnist-shaped 512-core net, plain path, batch 1, {args.plain_samples} samples "
-                               f"x {WINDOW} ticks per step", "l2": "flushed between timed steps (512 MiB write)",
-                   "path": "plain"},
+        "metric": METRIC, "value": samples_total / (ms_b * 1e-3), "unit": "samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 (fp16 0/1 and weight operands, fp32 exact accumulate)",
+        "data": "synthetic",
+        "synaptic_events_per_sec": br["events"] * ws / (ms_b * 1e-3),
+        "config": {"workload": f"mnist-shaped 512-core net (256x256 cores), batched path, {nb} samples x "
+                               f"{WINDOW} ticks per step", "path": "batched", "samples_per_step": nb,
+                   "l2": "working set (1 GiB potentials + 1 GiB scheduler rows) larger than L2",
+                   "parallelism": f"replicas x{ws} (samples sharded, no collective)"},
+        "plain": plain, "batched_over_plain": (samples_total / (ms_b * 1e-3)) / plain["samples_per_sec"],
         "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": e2e_n / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(xh.nbytes),
-                "d2h_bytes_per_step": int(ch.nbytes)},
-        "clocks": clk.summary(), "gpu_launches": int(pr["launches"]),
+        "e2e": {"value": e2e["value"] * ws, "unit": "samples/s", "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"]},
+        "clocks": clk.summary(), "gpu_launches": int(br["launches"]),
     }
     if rank == 0:
         print(json.dumps(line))

@@ -154,10 +154,11 @@ __device__ __forceinline__ uint32_t valid_mask(int n_valid, int first) {
     return k >= 32 ? 0xffffffffu : (k <= 0 ? 0u : ((1u << k) - 1u));
 }
 
-// Integer value of an fp32 that holds an integer of magnitude < 2^22
-// (adding 1.5 * 2^23 puts it in the low mantissa bits).
-__device__ __forceinline__ int f32_to_int_exact(uint32_t bits) {
-    return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+// For an fp32 holding an integer x with |x| < 2^22, adding 1.5 * 2^23 puts x
+// in the low mantissa bits: the result's bit pattern is 0x4B400000 + x.  The
+// caller subtracts the bias (folded into its leak constant).
+__device__ __forceinline__ int f32_bits_minus_bias(uint32_t bits) {
+    return __float_as_int(__uint_as_float(bits) + 12582912.0f);
 }
 
 template <typename VT>
@@ -187,6 +188,29 @@ __device__ __forceinline__ void load32(const VT *p, int (&v)[32]) {
     }
 }
 
+template <typename VT, int kVecs>
+__device__ __forceinline__ void unpack32(const uint4 (&q)[kVecs], int (&v)[32]) {
+    if constexpr (sizeof(VT) == 2) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v[8 * k + 2 * e] = (int)(int16_t)(w[e] & 0xFFFFu);
+                v[8 * k + 2 * e + 1] = (int)w[e] >> 16;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[4 * k] = (int)q[k].x;
+            v[4 * k + 1] = (int)q[k].y;
+            v[4 * k + 2] = (int)q[k].z;
+            v[4 * k + 3] = (int)q[k].w;
+        }
+    }
+}
+
 template <typename VT>
 __device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
     if constexpr (sizeof(VT) == 2) {
@@ -210,7 +234,7 @@ __device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
 // The tick kernel
 // ---------------------------------------------------------------------------
 
-template <typename VT>
+template <typename VT, int kNegReset>
 __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArgs a, const __grid_constant__ CUtensorMap wmap) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full[4], s_empty[4], acc_full[2], acc_empty[2];
@@ -221,20 +245,22 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     const int NH = a.NH, KB = a.KB, C = a.C, A = a.A, N = a.N, T = a.T;
     uint8_t *Wsm = base;                                   // [NH][KB] blocks of 128 rows x 128 B
     uint8_t *Ssm = Wsm + (size_t)NH * KB * kBlockBytes;    // [KB] blocks
-    uint4 *lut = reinterpret_cast<uint4 *>(Ssm + (size_t)KB * kBlockBytes);
+    uint2 *lut = reinterpret_cast<uint2 *>(Ssm + (size_t)KB * kBlockBytes);  // 16 x 8 B: one row of banks
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = (int)((long long)blockIdx.x * a.items / gridDim.x);
     const int i1 = (int)((long long)(blockIdx.x + 1) * a.items / gridDim.x);
     const int r0 = (int)(a.tick & (kRows - 1));
 
-    // 8 fp16 values (1.0 or 0.0) for every byte of spike bits.
-    for (int e = tid; e < 256; e += kThreads) {
-        uint32_t w[4];
+    // 4 fp16 values (1.0 or 0.0) for every nibble of spike bits.  The table is
+    // 128 bytes, so distinct entries sit in distinct banks and a warp's
+    // lookups never conflict.
+    if (tid < 16) {
+        uint32_t w[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            w[q] = (((e >> (2 * q)) & 1) ? 0x3C00u : 0u) | (((e >> (2 * q + 1)) & 1) ? 0x3C000000u : 0u);
-        lut[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int q = 0; q < 2; ++q)
+            w[q] = (((tid >> (2 * q)) & 1) ? 0x3C00u : 0u) | (((tid >> (2 * q + 1)) & 1) ? 0x3C000000u : 0u);
+        lut[tid] = make_uint2(w[0], w[1]);
     }
     if (tid == 0) {
         mbar_init(&bar_w, 1);
@@ -266,42 +292,78 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
 
     if (warp < kEpiWarps) {
         // ------------------------------------------------------------ epilogue
-        const int q = warp & 3, g = warp >> 2;
+        // Unit u = (neuron half h, 32-sample chunk cc); this warp owns units
+        // g*nu .. g*nu+nu-1 for TMEM lanes 32q..32q+31.  The potentials of the
+        // first kPre units are loaded before waiting for the accumulator and
+        // the rest are loaded kPre units ahead, so global latency overlaps
+        // the tensor-core work.
+        const int q = warp & 3, g = warp >> 2, nu = 2 * NH;
+        constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
+        constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;
         VT *Vg = reinterpret_cast<VT *>(a.V);
+        // Every unit of this warp is the same neuron (only the 32-sample chunk
+        // differs), so its parameters change only when the core does.
+        const int n = (NH == 2 ? g * 128 : 0) + q * 32 + lane;
+        int pc = -1;
+        int lam = 0, pth = 0, nth = 0, rst = 0;
+        uint2 dd = make_uint2(0u, 0u);
         for (int it = i0; it < i1; ++it) {
             const int li = it - i0, c = it / T, j = it % T, buf = li & 1;
+            if (c != pc) {
+                const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
+                lam = pr.x - 0x4B400000;  // folds the fp32 -> int bias of f32_bits_minus_bias
+                pth = pr.y;
+                nth = pr.z;
+                rst = pr.w;
+                dd = a.dst[(size_t)c * N + n];
+                pc = c;
+            }
+            const uint32_t kind = dest_kind(dd);
+            uint4 vb[kPre][kVecs];
+            auto vaddr = [&](int k) {
+                const int cc = (g * nu + k) & 3;
+                return reinterpret_cast<uint4 *>(Vg + ((((size_t)j * C + c) * 4 + cc) * N + n) * 32);
+            };
+#pragma unroll
+            for (int k = 0; k < kPre; ++k)
+                if (k < nu) {
+                    const uint4 *vp = vaddr(k);
+#pragma unroll
+                    for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e];
+                }
             if (!wait(&acc_full[buf], (li >> 1) & 1)) break;
             tc_fence_after();
             uint32_t n_sp = 0, n_pk = 0, n_out = 0;
-            for (int k = 0; k < 2 * NH; ++k) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k >= nu) break;
                 __syncwarp();
-                const int u = g * 2 * NH + k, h = u >> 2, cc = u & 3;
-                const int n = h * 128 + q * 32 + lane;
-                const size_t cn = (size_t)c * N + n;
-                const int4 pr = a.prm[cn];  // leak, pos_thr, neg_thr, reset
-                const size_t vbase = ((((size_t)j * C + c) * 4 + cc) * N + n) * 32;
+                const int u = g * nu + k, h = u >> 2, cc = u & 3;
                 int v[32];
-                load32<VT>(Vg + vbase, v);
+                unpack32<VT>(vb[k % kPre], v);
                 uint32_t d[32];
                 tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NH * 128 + h * 128 + cc * 32), d);
                 uint32_t mask = 0u;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const int x = v[i] + f32_to_int_exact(d[i]) + pr.x;
-                    const bool fire = x >= pr.y;
-                    int y = a.neg_mode ? (x < pr.z ? pr.w : x) : max(x, pr.z);
-                    y = fire ? pr.w : y;
+                    const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
+                    const bool fire = x >= pth;
+                    int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
+                    y = fire ? rst : y;
                     v[i] = y;
                     mask |= (fire ? 1u : 0u) << i;
                 }
-                store32<VT>(Vg + vbase, v);
+                store32<VT>(reinterpret_cast<VT *>(vaddr(k)), v);
+                if (k + kPre < nu) {
+                    const uint4 *vp = vaddr(k + kPre);
+#pragma unroll
+                    for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e];
+                }
                 a.spk[(((size_t)j * C + c) * 4 + cc) * N + n] = mask;
                 const uint32_t valid = valid_mask(a.n_valid, j * 128 + cc * 32);
                 const uint32_t live = mask & valid;
                 n_sp += __popc(live);
                 if (mask) {
-                    const uint2 dd = a.dst[cn];
-                    const uint32_t kind = dest_kind(dd);
                     if (kind == RANC_DEST_CORE) {
                         const uint32_t ax = dest_axon(dd);
                         const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
@@ -333,38 +395,76 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         }
     } else if (warp < kMmaWarp) {
         // ------------------------------------------------------------ producers
-        const int p = warp - kProdWarp0;
-        for (int it = i0; it < i1; ++it) {
+        // Warp p builds K-blocks kb0 = p/2 and kb0 + 2 (axon block 2kb + p%2
+        // of each).  Each lane keeps the input line of its axons in registers
+        // (-1: none, -2: several, read from the fan-in list) and loads the
+        // next item's scheduler words and input words while the tensor core
+        // works on the current item.
+        const int p = warp - kProdWarp0, kb0 = p >> 1;
+        const int ntask = (kb0 < KB ? 1 : 0) + (kb0 + 2 < KB ? 1 : 0);
+        int axn[2], line[2] = {-1, -1};
+        axn[0] = 32 * (2 * kb0 + (p & 1)) + lane;
+        axn[1] = 32 * (2 * (kb0 + 2) + (p & 1)) + lane;
+        int cur_core = -1;
+        uint4 R[2], I[2];
+        const bool inputs_now = a.tick < a.in_ticks;
+        auto fetch = [&](int it) {
+            const int c = it / T, j = it % T;
+            if (c != cur_core) {
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+                    if (t < ntask) {
+                        const int *fp = a.fin_ptr + (size_t)c * (A + 1) + axn[t];
+                        const int f0 = fp[0], cnt = fp[1] - f0;
+                        line[t] = cnt == 0 ? -1 : (cnt == 1 ? a.fin_line[f0] : -2);
+                    }
+                cur_core = c;
+            }
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                if (t < ntask) {
+                    R[t] = a.ring[(((size_t)j * C + c) * kRows + r0) * A + axn[t]];
+                    I[t] = (inputs_now && line[t] >= 0)
+                               ? a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + line[t]]
+                               : make_uint4(0u, 0u, 0u, 0u);
+                }
+        };
+        if (i0 < i1 && ntask > 0) fetch(i0);
+        for (int it = i0; it < i1 && ntask > 0; ++it) {
             const int li = it - i0, c = it / T, j = it % T;
             bool ok = true;
             unsigned long long ev = 0;
-            for (int kb = p >> 1; kb < KB; kb += 2) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (t >= ntask) break;
+                const int kb = kb0 + 2 * t, ab = 2 * kb + (p & 1), ax = axn[t];
                 if (!wait(&s_empty[kb], (li & 1) ^ 1)) {
                     ok = false;
                     break;
                 }
-                const int ab = 2 * kb + (p & 1);
-                const int ax = 32 * ab + lane;
-                uint4 *rowp = a.ring + (((size_t)j * C + c) * kRows + r0) * A + ax;
-                uint4 R = *rowp;
-                *rowp = make_uint4(0u, 0u, 0u, 0u);
-                if (a.tick < a.in_ticks) {
+                uint4 Rt = R[t];
+                Rt.x |= I[t].x;
+                Rt.y |= I[t].y;
+                Rt.z |= I[t].z;
+                Rt.w |= I[t].w;
+                if (line[t] == -2 && inputs_now) {
                     const int *fp = a.fin_ptr + (size_t)c * (A + 1) + ax;
                     for (int k = fp[0]; k < fp[1]; ++k) {
-                        const uint4 I = a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + a.fin_line[k]];
-                        R.x |= I.x;
-                        R.y |= I.y;
-                        R.z |= I.z;
-                        R.w |= I.w;
+                        const uint4 In = a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + a.fin_line[k]];
+                        Rt.x |= In.x;
+                        Rt.y |= In.y;
+                        Rt.z |= In.z;
+                        Rt.w |= In.w;
                     }
                 }
+                a.ring[(((size_t)j * C + c) * kRows + r0) * A + ax] = make_uint4(0u, 0u, 0u, 0u);
                 const uint32_t od = a.outdeg[(size_t)c * A + ax];
-                ev += (unsigned long long)od * (__popc(R.x & valid_mask(a.n_valid, j * 128)) +
-                                                __popc(R.y & valid_mask(a.n_valid, j * 128 + 32)) +
-                                                __popc(R.z & valid_mask(a.n_valid, j * 128 + 64)) +
-                                                __popc(R.w & valid_mask(a.n_valid, j * 128 + 96)));
+                ev += (unsigned long long)od * (__popc(Rt.x & valid_mask(a.n_valid, j * 128)) +
+                                                __popc(Rt.y & valid_mask(a.n_valid, j * 128 + 32)) +
+                                                __popc(Rt.z & valid_mask(a.n_valid, j * 128 + 64)) +
+                                                __popc(Rt.w & valid_mask(a.n_valid, j * 128 + 96)));
                 uint8_t *blk = Ssm + (size_t)kb * kBlockBytes;
-                const uint32_t words[4] = {R.x, R.y, R.z, R.w};
+                const uint32_t words[4] = {Rt.x, Rt.y, Rt.z, Rt.w};
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                     const uint32_t y = transpose32(words[w], lane);
@@ -372,7 +472,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
                         const int chunk = (ab & 1) * 4 + qq;
-                        *reinterpret_cast<uint4 *>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) = lut[(y >> (8 * qq)) & 0xFFu];
+                        const uint2 lo = lut[(y >> (8 * qq)) & 0xFu], hi = lut[(y >> (8 * qq + 4)) & 0xFu];
+                        *reinterpret_cast<uint4 *>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) =
+                            make_uint4(lo.x, lo.y, hi.x, hi.y);
                     }
                 }
                 fence_async_smem();
@@ -380,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 if (lane == 0) mbar_arrive(&s_full[kb]);
             }
             if (!ok) break;
+            if (it + 1 < i1) fetch(it + 1);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
             if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
@@ -411,6 +514,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
             if (it + 1 < i1) {
                 const int c1 = (it + 1) / T, j1 = (it + 1) % T;
                 prefetch_l2(reinterpret_cast<const uint8_t *>(a.V) + ((size_t)j1 * C + c1) * vtile, (uint32_t)vtile);
+            }
+            if (it + 2 < i1) {
+                const int c2 = (it + 2) / T, j2 = (it + 2) % T;
+                prefetch_l2(a.ring + (((size_t)j2 * C + c2) * kRows + r0) * A, (uint32_t)A * 16u);
             }
             if (!wait(&acc_empty[buf], ((li >> 1) & 1) ^ 1)) break;
             tc_fence_after();
@@ -684,9 +791,13 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         why = "cuTensorMapEncodeTiled failed";
         return cudaErrorInvalidValue;
     }
-    e = v16 ? cudaFuncSetAttribute(batched_tick_kernel<int16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem)
-            : cudaFuncSetAttribute(batched_tick_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs->smem);
-    if (e != cudaSuccess) why = "kernel shared-memory attribute";
+    const int sm = (int)bs->smem;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 0>, at, sm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 1>, at, sm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(batched_tick_kernel<int, 0>, at, sm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(batched_tick_kernel<int, 1>, at, sm)) != cudaSuccess)
+        why = "kernel shared-memory attribute";
     return e;
 }
 
@@ -700,10 +811,9 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.inT = bs->inT; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
     a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
     const int grid = std::min(bs->n_sm, a.items);
-    if (sim->v16)
-        batched_tick_kernel<int16_t><<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
-    else
-        batched_tick_kernel<int><<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
+    auto kern = sim->v16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
+                         : (sim->neg_mode ? batched_tick_kernel<int, 1> : batched_tick_kernel<int, 0>);
+    kern<<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
     return cudaGetLastError();
 }
 
