@@ -203,6 +203,10 @@ int fold_timing(ranc_sim *sim) {
 
 int step_ticks(ranc_sim *sim, int n_ticks) {
     for (int t = 0; t < n_ticks; t++) {
+        if (sim->path == RANC_PATH_BATCHED) {
+            cudaError_t ei = batched_inject(sim);
+            if (ei != cudaSuccess) return fail(sim, RANC_ECUDA, "input injection: %s", cudaGetErrorString(ei));
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (sim->timing) {
             if (sim->ev_used + 2 > 4096) {

@@ -396,40 +396,27 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     } else if (warp < kMmaWarp) {
         // ------------------------------------------------------------ producers
         // Warp p builds K-blocks kb0 = p/2 and kb0 + 2 (axon block 2kb + p%2
-        // of each).  Each lane keeps the input line of its axons in registers
-        // (-1: none, -2: several, read from the fan-in list) and loads the
-        // next item's scheduler words and input words while the tensor core
-        // works on the current item.
+        // of each).  Input lines were already ORed into the scheduler rows
+        // (inject_inputs), so a row is the whole active-axon set of its tick.
+        // Rows are loaded into registers three items ahead of their use.
         const int p = warp - kProdWarp0, kb0 = p >> 1;
         const int ntask = (kb0 < KB ? 1 : 0) + (kb0 + 2 < KB ? 1 : 0);
-        int axn[2], line[2] = {-1, -1};
+        int axn[2];
         axn[0] = 32 * (2 * kb0 + (p & 1)) + lane;
         axn[1] = 32 * (2 * (kb0 + 2) + (p & 1)) + lane;
-        int cur_core = -1;
-        uint4 R[2], I[2];
-        const bool inputs_now = a.tick < a.in_ticks;
-        auto fetch = [&](int it) {
+        uint4 R0[2], R1[2], R2[2];
+        auto rows = [&](int it, uint4 (&R)[2]) {
+            if (it >= i1) return;
             const int c = it / T, j = it % T;
-            if (c != cur_core) {
-#pragma unroll
-                for (int t = 0; t < 2; ++t)
-                    if (t < ntask) {
-                        const int *fp = a.fin_ptr + (size_t)c * (A + 1) + axn[t];
-                        const int f0 = fp[0], cnt = fp[1] - f0;
-                        line[t] = cnt == 0 ? -1 : (cnt == 1 ? a.fin_line[f0] : -2);
-                    }
-                cur_core = c;
-            }
 #pragma unroll
             for (int t = 0; t < 2; ++t)
-                if (t < ntask) {
-                    R[t] = a.ring[(((size_t)j * C + c) * kRows + r0) * A + axn[t]];
-                    I[t] = (inputs_now && line[t] >= 0)
-                               ? a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + line[t]]
-                               : make_uint4(0u, 0u, 0u, 0u);
-                }
+                if (t < ntask) R[t] = a.ring[(((size_t)j * C + c) * kRows + r0) * A + axn[t]];
         };
-        if (i0 < i1 && ntask > 0) fetch(i0);
+        if (ntask > 0) {
+            rows(i0, R0);
+            rows(i0 + 1, R1);
+            rows(i0 + 2, R2);
+        }
         for (int it = i0; it < i1 && ntask > 0; ++it) {
             const int li = it - i0, c = it / T, j = it % T;
             bool ok = true;
@@ -442,21 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     ok = false;
                     break;
                 }
-                uint4 Rt = R[t];
-                Rt.x |= I[t].x;
-                Rt.y |= I[t].y;
-                Rt.z |= I[t].z;
-                Rt.w |= I[t].w;
-                if (line[t] == -2 && inputs_now) {
-                    const int *fp = a.fin_ptr + (size_t)c * (A + 1) + ax;
-                    for (int k = fp[0]; k < fp[1]; ++k) {
-                        const uint4 In = a.inT[((size_t)j * a.in_ticks + a.tick) * a.Lpad + a.fin_line[k]];
-                        Rt.x |= In.x;
-                        Rt.y |= In.y;
-                        Rt.z |= In.z;
-                        Rt.w |= In.w;
-                    }
-                }
+                const uint4 Rt = R0[t];
                 a.ring[(((size_t)j * C + c) * kRows + r0) * A + ax] = make_uint4(0u, 0u, 0u, 0u);
                 const uint32_t od = a.outdeg[(size_t)c * A + ax];
                 ev += (unsigned long long)od * (__popc(Rt.x & valid_mask(a.n_valid, j * 128)) +
@@ -482,7 +455,12 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 if (lane == 0) mbar_arrive(&s_full[kb]);
             }
             if (!ok) break;
-            if (it + 1 < i1) fetch(it + 1);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                R0[t] = R1[t];
+                R1[t] = R2[t];
+            }
+            rows(it + 3, R2);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
             if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
@@ -585,6 +563,36 @@ __global__ void transpose_inputs(const uint32_t *x, int n_samples, int ticks, in
 
 // Canonical copies of samples [b0, b0 + nb): v [nb][C][N], spk [nb][C][N/32],
 // ring [nb][C][16][A/32] (ring may be NULL).
+// ORs the input lines of ticks [tau0, tau1) into scheduler rows tau mod 16
+// for every tile: ring[j][c][tau&15][a] |= OR of inT[j][tau][line] over the
+// lines that drive (c, a) (Alg. 1: the packets of the current tick are
+// written into the scheduler before the neuron block).
+__global__ void inject_inputs(const uint4 *inT, int in_ticks, int Lpad, int tau0, int tau1, int T, int C, int A,
+                              const int *inj_ca, const int *inj_ptr, const int *fin_line, int n_pairs, uint4 *ring) {
+    const long long total = (long long)(tau1 - tau0) * T * n_pairs;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total; f += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(f % n_pairs);
+        const int j = (int)((f / n_pairs) % T);
+        const int tau = tau0 + (int)(f / n_pairs / T);
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        for (int e = inj_ptr[k]; e < inj_ptr[k + 1]; ++e) {
+            const uint4 I = inT[((size_t)j * in_ticks + tau) * Lpad + fin_line[e]];
+            w.x |= I.x;
+            w.y |= I.y;
+            w.z |= I.z;
+            w.w |= I.w;
+        }
+        const int c = inj_ca[k] / A, ax = inj_ca[k] % A;
+        uint4 *r = ring + (((size_t)j * C + c) * kRows + (tau & (kRows - 1))) * A + ax;
+        uint4 o = *r;
+        o.x |= w.x;
+        o.y |= w.y;
+        o.z |= w.z;
+        o.w |= w.w;
+        *r = o;
+    }
+}
+
 template <typename VT>
 __global__ void export_state(const VT *Vb, const uint32_t *spkb, const uint32_t *ringb, int b0, int nb, int C, int N,
                              int A, int *v, uint32_t *spk, uint32_t *ring) {
@@ -662,6 +670,8 @@ struct Batched {
     size_t smem = 0;
     __half *wfold = nullptr;
     int *fin_ptr = nullptr, *fin_line = nullptr;
+    int *inj_ca = nullptr, *inj_ptr = nullptr;  // (core, axon) pairs fed by input lines, CSR into fin_line
+    int n_pairs = 0;
     uint16_t *outdeg = nullptr;
     uint4 *inT = nullptr;
     size_t inT_cap = 0;
@@ -750,6 +760,24 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         }
         if (fline.empty()) fline.push_back(0);
     }
+    std::vector<int> inj_ca, inj_ptr(1, 0);
+    for (int c = 0; c < C; c++)
+        for (int ax = 0; ax < A; ax++) {
+            const int f0 = fptr[(size_t)c * (A + 1) + ax], f1 = fptr[(size_t)c * (A + 1) + ax + 1];
+            if (f1 > f0) {
+                inj_ca.push_back(c * A + ax);
+                inj_ptr.push_back(f1);
+            }
+        }
+    // inj_ptr holds end offsets; make it a CSR with the start of the first pair
+    std::vector<int> inj_csr(inj_ca.size() + 1, 0);
+    for (size_t k = 0; k < inj_ca.size(); k++) {
+        const int c = inj_ca[k] / A, ax = inj_ca[k] % A;
+        inj_csr[k] = fptr[(size_t)c * (A + 1) + ax];
+        inj_csr[k + 1] = fptr[(size_t)c * (A + 1) + ax + 1];
+    }
+    bs->n_pairs = (int)inj_ca.size();
+    if (inj_ca.empty()) inj_ca.push_back(0);
     const size_t vsz = v16 ? 2 : 4;
     if (cudaMalloc(&bs->wfold, wf.size() * 2) != cudaSuccess || cudaMalloc(&bs->outdeg, od.size() * 2) != cudaSuccess ||
         cudaMalloc(&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
@@ -766,7 +794,11 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     if ((e = cudaMemcpy(bs->wfold, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->fin_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&bs->inj_ca, inj_ca.size() * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&bs->inj_ptr, inj_csr.size() * 4)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->inj_ca, inj_ca.data(), inj_ca.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->inj_ptr, inj_csr.data(), inj_csr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         why = "copy of the batched network arrays";
         return e;
     }
@@ -852,6 +884,19 @@ cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n
     return cudaGetLastError();
 }
 
+// Input lines of the tick about to be simulated into its scheduler row (all
+// deliveries for that row happened in earlier ticks, so the row is final).
+cudaError_t batched_inject(ranc_sim *sim) {
+    Batched *bs = B_of(sim);
+    if (!bs->inT || bs->n_pairs == 0 || sim->tick >= sim->in_ticks) return cudaSuccess;
+    const long long total = (long long)sim->T * bs->n_pairs;
+    inject_inputs<<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+        bs->inT, sim->in_ticks, bs->Lpad, (int)sim->tick, (int)sim->tick + 1, sim->T, sim->C, sim->A, bs->inj_ca,
+        bs->inj_ptr, bs->fin_line, bs->n_pairs, reinterpret_cast<uint4 *>(sim->ring));
+    sim->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk, uint32_t *ring) {
     const long long total = (long long)nb * sim->C * sim->N + (long long)nb * sim->C * (sim->N / 32) +
                             (ring ? (long long)nb * sim->C * kRows * (sim->A / 32) : 0);
@@ -881,7 +926,7 @@ cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *s
 void batched_teardown(ranc_sim *sim) {
     Batched *bs = B_of(sim);
     if (!bs) return;
-    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT};
+    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT, bs->inj_ca, bs->inj_ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete bs;
