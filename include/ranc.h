@@ -157,6 +157,27 @@ int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint64_t *diges
  * RANC_EINVAL when the range leaves the batch.  Synchronous. */
 int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes);
 
+/* Allocation-free variant of ranc_read_sample_state (the paper has no
+ * counterpart; this entry point exists for callers of this library).
+ * ranc_read_sample_state on the batched path allocates and frees temporary
+ * device buffers on every call.  Some callers cannot do that: applications
+ * whose own allocator owns the device memory and forbids allocations outside
+ * it, real-time loops that must not allocate (or free, which synchronises the
+ * device) after start-up, and callers held to a fixed device-memory budget.
+ * This variant converts the state in a fixed scratch array compiled into the
+ * library (8 MiB, held by every GPU that loads the library until the process
+ * exits) and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - nb * C * N * 4 * (1 + 1/32) bytes must fit in the 8 MiB (512 cores x
+ *     256 neurons: at most 15 samples per call); larger ranges return
+ *     RANC_EINVAL with the limit in ranc_last_error.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (once per device); make that first call before any stream capture.
+ *   - All calls in the process share the one array: calls that overlap on the
+ *     GPU (other streams or threads) race.  Every call rewrites the part it
+ *     uses, so no call depends on what an earlier call left there.
+ * Outputs, meaning and synchronisation are those of ranc_read_sample_state. */
+int ranc_read_sample_state_noalloc(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes);
+
 /* counters[RANC_N_COUNTERS] summed over the batch since the last ranc_reset
  * (ranc_run_samples keeps accumulating across its windows).  Synchronous. */
 int ranc_read_counters(ranc_sim *sim, uint64_t *counters);

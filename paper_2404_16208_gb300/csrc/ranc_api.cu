@@ -557,6 +557,28 @@ extern "C" int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int
     return sync_and_check(sim);
 }
 
+extern "C" int ranc_read_sample_state_noalloc(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes) {
+    CHECK_LIVE(sim);
+    if (b0 < 0 || nb < 0 || (long long)b0 + nb > sim->B) return fail(sim, RANC_EINVAL, "sample range outside the batch");
+    const size_t per_v = (size_t)sim->C * sim->N, per_s = (size_t)sim->C * (sim->N / 32);
+    if ((size_t)nb * (per_v + per_s) * 4 > kNoAllocScratchBytes)
+        return fail(sim, RANC_EINVAL, "%d samples need %zu bytes of scratch; the allocation-free read holds at most %zu",
+                    nb, (size_t)nb * (per_v + per_s) * 4, kNoAllocScratchBytes);
+    if (nb == 0) return RANC_OK;
+    if (sim->path == RANC_PATH_PLAIN) {  // the state already has the canonical layout: copy it out
+        if (v)
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, (int *)sim->V + (size_t)b0 * per_v, (size_t)nb * per_v * 4,
+                                              cudaMemcpyDeviceToHost, sim->stream));
+        if (spikes)
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, sim->spk + (size_t)b0 * per_s, (size_t)nb * per_s * 4,
+                                              cudaMemcpyDeviceToHost, sim->stream));
+        return sync_and_check(sim);
+    }
+    cudaError_t e = batched_export_noalloc(sim, b0, nb, v, spikes);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "allocation-free state read: %s", cudaGetErrorString(e));
+    return sync_and_check(sim);
+}
+
 extern "C" int ranc_read_counters(ranc_sim *sim, uint64_t *counters) {
     CHECK_LIVE(sim);
     if (!counters) return fail(sim, RANC_EINVAL, "counters is NULL");

@@ -36,6 +36,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ranc_internal.cuh"
@@ -921,6 +922,57 @@ cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *s
             (int *)sim->V, sim->spk, sim->ring, sim->B, sim->T, sim->C, sim->N, sim->A, v, spk, ring);
     sim->launches++;
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free read of a sample range (see ranc_read_sample_state_noalloc).
+// The canonical copies go to a fixed device array that every GPU loading this
+// library holds until the process exits; no call allocates device memory.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current (a host-side use of the symbol is not a device
+// address).
+cudaError_t noalloc_scratch(int device, void **ptr) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        int cur = 0;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (cur != device) cudaSetDevice(cur);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *ptr = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, uint32_t *spk_host) {
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(sim->device, &scratch);
+    if (e != cudaSuccess) return e;
+    const size_t per_v = (size_t)sim->C * sim->N, per_s = (size_t)sim->C * (sim->N / 32);
+    int *v = static_cast<int *>(scratch);
+    uint32_t *spk = reinterpret_cast<uint32_t *>(v + (size_t)nb * per_v);
+    if ((e = launch_batched_export(sim, b0, nb, v, spk, nullptr)) != cudaSuccess) return e;
+    if (v_host && (e = cudaMemcpyAsync(v_host, v, (size_t)nb * per_v * 4, cudaMemcpyDeviceToHost, sim->stream)) != cudaSuccess)
+        return e;
+    if (spk_host &&
+        (e = cudaMemcpyAsync(spk_host, spk, (size_t)nb * per_s * 4, cudaMemcpyDeviceToHost, sim->stream)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
 void batched_teardown(ranc_sim *sim) {

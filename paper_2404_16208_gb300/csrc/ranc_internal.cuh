@@ -15,6 +15,7 @@ constexpr int kRows = RANC_ROWS;     // scheduler rows (Sec. III-E); delays 1..1
 constexpr int kMaxTypes = 8;         // weight slots per neuron
 constexpr int kMaxWords = 32;        // axons/32 and neurons/32 upper bound (1024)
 constexpr int kTileS = 128;          // samples per tensor-core tile (batched path)
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // static scratch of the allocation-free read
 
 // Device error word values (set by kernels, read by synchronous host calls).
 enum : int { kErrNone = 0, kErrTimeout = 1, kErrBounds = 2 };
@@ -133,5 +134,6 @@ cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, u
                                   uint32_t *ring_canon);
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *spk_canon,
                                   const uint32_t *ring_canon);
+cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, uint32_t *spk_host);
 void batched_teardown(ranc_sim *sim);
 }  // namespace ranc

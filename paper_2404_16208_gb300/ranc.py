@@ -20,7 +20,8 @@ RANC_PATH_PLAIN, RANC_PATH_BATCHED = 0, 1
 RANC_MEM_HOST, RANC_MEM_DEVICE = 0, 1
 COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
 EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
-            "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_counters", "ranc_get_tick", "ranc_reset",
+            "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
+            "ranc_read_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
             "ranc_read_kernel_timing", "ranc_launch_count", "ranc_destroy", "ranc_last_error")
 
@@ -59,6 +60,7 @@ def load_library(path=LIB_PATH):
         "ranc_read_outputs_device": ([vp, vp], C.c_int),
         "ranc_read_state": ([vp, vp, vp, u64p], C.c_int),
         "ranc_read_sample_state": ([vp, i32, i32, vp, vp], C.c_int),
+        "ranc_read_sample_state_noalloc": ([vp, i32, i32, vp, vp], C.c_int),
         "ranc_read_counters": ([vp, u64p], C.c_int),
         "ranc_get_tick": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_reset": ([vp], C.c_int),
@@ -147,6 +149,15 @@ def ranc_read_sample_state(h, b0, nb, n_cores, neurons):
     v = np.zeros((nb, n_cores, neurons), np.int32)
     s = np.zeros((nb, n_cores, neurons // 32), np.uint32)
     _check(_lib.ranc_read_sample_state(h, int(b0), int(nb), _p(v), _p(s)), h)
+    return v, s
+
+
+def ranc_read_sample_state_noalloc(h, b0, nb, n_cores, neurons):
+    """Same result as ranc_read_sample_state, through the entry point that
+    allocates no device memory (bounded sample range)."""
+    v = np.zeros((nb, n_cores, neurons), np.int32)
+    s = np.zeros((nb, n_cores, neurons // 32), np.uint32)
+    _check(_lib.ranc_read_sample_state_noalloc(h, int(b0), int(nb), _p(v), _p(s)), h)
     return v, s
 
 
