@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -20,9 +21,14 @@
 
 using namespace ranc;
 
+namespace ranc {
+cudaError_t dev_alloc(void **p, size_t bytes);
+}
+
 namespace {
 
 thread_local std::string g_create_error;
+thread_local long long g_alloc_budget = -1;  // < 0: no fault injection
 
 int fail(ranc_sim *sim, int code, const char *fmt, ...) {
     char buf[512];
@@ -56,7 +62,7 @@ template <typename T>
 cudaError_t dmalloc(T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+    return dev_alloc(reinterpret_cast<void **>(p), n * sizeof(T));
 }
 
 template <typename T>
@@ -228,6 +234,7 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
             a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon;
             a.inputs = sim->in_override ? sim->in_override : sim->inputs;
             a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+            a.stall_test = sim->stall_test;
             e = launch_plain_tick(a, sim->stream);
         } else {
             BatchedArgs a{};
@@ -372,6 +379,18 @@ int read_counters4(ranc_sim *sim, unsigned long long *h4) {
 
 }  // namespace
 
+cudaError_t ranc::dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (g_alloc_budget == 0) return cudaErrorMemoryAllocation;
+    if (g_alloc_budget > 0) g_alloc_budget--;
+    return cudaMalloc(p, bytes);
+}
+
+void ranc::fault_alloc_arm_from_env() {
+    const char *v = getenv("RANC_FAULT_ALLOC_AFTER");
+    g_alloc_budget = (v && *v) ? atoll(v) : -1;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -382,6 +401,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     std::vector<int> core_at;
     std::string why;
     if (!validate(d, batch, path, core_at, why)) return fail(nullptr, RANC_EINVAL, "%s", why.c_str());
+    fault_alloc_arm_from_env();
     ranc_sim *sim = new (std::nothrow) ranc_sim();
     if (!sim) return fail(nullptr, RANC_ENOMEM, "host allocation");
     const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types, AW = A / 32;
@@ -390,7 +410,12 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     sim->in_words = (d->n_inputs + 31) / 32; sim->weight_bits = d->weight_bits;
     sim->stream = static_cast<cudaStream_t>(cuda_stream);
     sim->n_valid = batch;
+    {
+        const char *st = getenv("RANC_TEST_STALL_WAIT");
+        sim->stall_test = (st && *st && *st != '0') ? 1 : 0;
+    }
     auto abort_create = [&](int code, const std::string &msg) {
+        g_alloc_budget = -1;
         g_create_error = msg;
         free_all(sim);
         delete sim;
@@ -474,6 +499,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
         std::string msg = sim->last_error;
         return abort_create(rc, msg);
     }
+    g_alloc_budget = -1;
     *out = sim;
     return RANC_OK;
 }
@@ -598,6 +624,7 @@ extern "C" int ranc_get_tick(const ranc_sim *sim, int64_t *tick) {
 
 extern "C" int ranc_reset(ranc_sim *sim) {
     if (!sim) return RANC_EINVAL;
+    sim->stall_test = 0;  // a stall-test handle runs normally once reset
     if (sim->sticky) {
         cudaError_t e = cudaStreamSynchronize(sim->stream);
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "device unusable: %s", cudaGetErrorString(e));

@@ -780,14 +780,14 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     bs->n_pairs = (int)inj_ca.size();
     if (inj_ca.empty()) inj_ca.push_back(0);
     const size_t vsz = v16 ? 2 : 4;
-    if (cudaMalloc(&bs->wfold, wf.size() * 2) != cudaSuccess || cudaMalloc(&bs->outdeg, od.size() * 2) != cudaSuccess ||
-        cudaMalloc(&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
-        cudaMalloc(&bs->fin_line, fline.size() * 4) != cudaSuccess ||
-        cudaMalloc(&sim->V, (size_t)sim->T * C * 4 * N * 32 * vsz) != cudaSuccess ||
-        cudaMalloc(&sim->ring, (size_t)sim->T * C * kRows * A * 16) != cudaSuccess ||
-        cudaMalloc(&sim->spk, (size_t)sim->T * C * 4 * N * 4) != cudaSuccess ||
-        cudaMalloc(&sim->out, (size_t)sim->B_pad * sim->n_outputs * 4) != cudaSuccess ||
-        cudaMalloc(&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess) {
+    if (dev_alloc((void **)&bs->wfold, wf.size() * 2) != cudaSuccess || dev_alloc((void **)&bs->outdeg, od.size() * 2) != cudaSuccess ||
+        dev_alloc((void **)&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
+        dev_alloc((void **)&bs->fin_line, fline.size() * 4) != cudaSuccess ||
+        dev_alloc((void **)&sim->V, (size_t)sim->T * C * 4 * N * 32 * vsz) != cudaSuccess ||
+        dev_alloc((void **)&sim->ring, (size_t)sim->T * C * kRows * A * 16) != cudaSuccess ||
+        dev_alloc((void **)&sim->spk, (size_t)sim->T * C * 4 * N * 4) != cudaSuccess ||
+        dev_alloc((void **)&sim->out, (size_t)sim->B_pad * sim->n_outputs * 4) != cudaSuccess ||
+        dev_alloc((void **)&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess) {
         why = "device allocation of the batched state failed";
         return cudaErrorMemoryAllocation;
     }
@@ -796,8 +796,8 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->fin_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMalloc(&bs->inj_ca, inj_ca.size() * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&bs->inj_ptr, inj_csr.size() * 4)) != cudaSuccess ||
+        (e = dev_alloc((void **)&bs->inj_ca, inj_ca.size() * 4)) != cudaSuccess ||
+        (e = dev_alloc((void **)&bs->inj_ptr, inj_csr.size() * 4)) != cudaSuccess ||
         (e = cudaMemcpy(bs->inj_ca, inj_ca.data(), inj_ca.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->inj_ptr, inj_csr.data(), inj_csr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         why = "copy of the batched network arrays";
@@ -875,7 +875,7 @@ cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n
         if (bs->inT) cudaFree(bs->inT);
         bs->inT = nullptr;
         bs->inT_cap = 0;
-        if (cudaMalloc(&bs->inT, need * 16) != cudaSuccess) return cudaErrorMemoryAllocation;
+        if (dev_alloc((void **)&bs->inT, need * 16) != cudaSuccess) return cudaErrorMemoryAllocation;
         bs->inT_cap = need;
     }
     const long long threads = (long long)sim->T * n_ticks * sim->in_words * 4 * 32;

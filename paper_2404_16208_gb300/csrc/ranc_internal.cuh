@@ -46,6 +46,7 @@ struct PlainArgs {
     uint32_t *out;               // [B][n_out]
     unsigned long long *cnt;     // [B][C][4]    spikes, packets, outputs, synaptic events
     int *err;
+    int stall_test;              // test only: CTA (0, 0) waits on an mbarrier nothing arrives on
 };
 
 // Batched-path device layout (one tile = kTileS samples, sample-minor bits).
@@ -115,8 +116,17 @@ struct ranc_sim {
     long long timed_launches = 0;
 
     int sticky = 0;
+    int stall_test = 0;                  // RANC_TEST_STALL_WAIT (failure-detection tests)
     std::string last_error;
 };
+
+namespace ranc {
+// Device allocation used by every part of the library.  RANC_FAULT_ALLOC_AFTER=n
+// (read by ranc_create) makes the (n+1)-th allocation of that create fail, so
+// tests can check that every failure path returns RANC_ENOMEM without leaks.
+cudaError_t dev_alloc(void **p, size_t bytes);
+void fault_alloc_arm_from_env();
+}  // namespace ranc
 
 namespace ranc {
 // Implemented in ranc_plain.cu

@@ -62,7 +62,18 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
             }
         }
     }
-    const bool ok = mbar_wait_bounded(&bar, 0);
+    bool ok = mbar_wait_bounded(&bar, 0);
+    if (a.stall_test && blockIdx.x == 0 && blockIdx.y == 0) {
+        // Failure-detection test: a barrier that never completes; the bounded
+        // wait must give up and report, not hang.
+        __shared__ __align__(8) uint64_t never;
+        if (n == 0) {
+            mbar_init(&never, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        ok = ok && mbar_wait_bounded(&never, 0);
+    }
     if (__syncthreads_or(!ok)) {
         if (n == 0) atomicExch(a.err, kErrTimeout);
         mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits

@@ -1,0 +1,77 @@
+"""Failure detection without any GPU fault.
+
+* A test-only flag (RANC_TEST_STALL_WAIT) makes one CTA of the plain tick
+  kernel wait on an mbarrier that nothing arrives on.  The bounded wait must
+  give up after its limit, the next synchronising call must return
+  RANC_ETIMEOUT, later calls RANC_ESTATE, and ranc_reset must bring the handle
+  back to correct results.
+* RANC_FAULT_ALLOC_AFTER=n makes the (n+1)-th device allocation of a create
+  fail: every such create must return RANC_ENOMEM and free what it took.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+import ranc_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ranc():
+    from paper_2404_16208_gb300 import build_library
+    build_library()
+    from paper_2404_16208_gb300 import ranc as mod
+    return mod
+
+
+def test_bounded_wait_gives_up_and_reset_recovers(ranc, oracle_mod, monkeypatch):
+    net = W.tiny_5core()
+    monkeypatch.setenv("RANC_TEST_STALL_WAIT", "1")
+    sim = ranc.Sim(net, 2, ranc.RANC_PATH_PLAIN)
+    monkeypatch.delenv("RANC_TEST_STALL_WAIT")
+    t0 = time.time()
+    sim.step(1)
+    with pytest.raises(ranc.RancError) as ei:
+        sim.outputs()
+    assert ei.value.code == ranc.RANC_ETIMEOUT
+    assert time.time() - t0 < 20
+    with pytest.raises(ranc.RancError) as ei:
+        sim.step(1)
+    assert ei.value.code == ranc.RANC_ESTATE
+    sim.reset()
+    x = W.rate_coded_inputs(5, 2, 8, 784, 0.15)
+    sim.load_inputs(x)
+    sim.step(9)
+    ref = oracle_mod.run(net, x, 9)
+    np.testing.assert_array_equal(sim.outputs(), ref["out"])
+    np.testing.assert_array_equal(sim.state()[0], ref["v"])
+    sim.close()
+
+
+@pytest.mark.parametrize("path", [0, 1], ids=["plain", "batched"])
+def test_allocation_failures_return_enomem_without_leaks(ranc, monkeypatch, path):
+    import torch
+    torch.cuda.init()
+    net = W.tiny_5core()
+    # A first create loads the library's device code and its static arrays,
+    # which stay resident; the baseline is taken after that.
+    ranc.ranc_destroy(ranc.ranc_create(net, 256, path))
+    free0 = torch.cuda.mem_get_info()[0]
+    succeeded_at = None
+    for k in range(0, 64):
+        monkeypatch.setenv("RANC_FAULT_ALLOC_AFTER", str(k))
+        try:
+            h = ranc.ranc_create(net, 256, path)
+        except ranc.RancError as e:
+            assert e.code == ranc.RANC_ENOMEM, str(e)
+            assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20), k
+            continue
+        succeeded_at = k
+        ranc.ranc_destroy(h)
+        break
+    monkeypatch.delenv("RANC_FAULT_ALLOC_AFTER")
+    assert succeeded_at is not None and succeeded_at >= 10
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
