@@ -45,10 +45,9 @@
 namespace ranc {
 namespace {
 
-constexpr int kThreads = 416;
-constexpr int kEpiWarps = 8;
-constexpr int kProdWarp0 = 8;
-constexpr int kMmaWarp = 12;
+constexpr int kWorkers = 16;                 // warps 0-15: operand build + epilogue
+constexpr int kMmaWarp = 16;                 // warp 16: TMEM, TMA, MMA issue
+constexpr int kThreads = (kWorkers + 1) * 32;
 constexpr uint32_t kBlockBytes = 128u * 128u;  // 128 rows x 64 fp16 = one swizzled K-block
 
 struct TickArgs {
@@ -114,7 +113,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ __attribute__((unused)) void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -122,6 +121,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -212,6 +220,51 @@ __device__ __forceinline__ void unpack32(const uint4 (&q)[kVecs], int (&v)[32]) 
     }
 }
 
+// Potentials hf*16 .. hf*16+15 of one 32-sample unit held as 16-byte vectors.
+template <typename VT, int kVecs>
+__device__ __forceinline__ void unpack16(const uint4 (&q)[kVecs], int hf, int (&v)[16]) {
+    if constexpr (sizeof(VT) == 2) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint4 u = q[hf * 2 + k];
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v[8 * k + 2 * e] = (int)(int16_t)(w[e] & 0xFFFFu);
+                v[8 * k + 2 * e + 1] = (int)w[e] >> 16;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint4 u = q[hf * 4 + k];
+            v[4 * k] = (int)u.x;
+            v[4 * k + 1] = (int)u.y;
+            v[4 * k + 2] = (int)u.z;
+            v[4 * k + 3] = (int)u.w;
+        }
+    }
+}
+
+template <typename VT>
+__device__ __forceinline__ void store16(uint4 *p, int hf, const int (&v)[16]) {
+    if constexpr (sizeof(VT) == 2) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                w[e] = ((uint32_t)v[8 * k + 2 * e] & 0xFFFFu) | ((uint32_t)v[8 * k + 2 * e + 1] << 16);
+            p[hf * 2 + k] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            p[hf * 4 + k] = make_uint4((uint32_t)v[4 * k], (uint32_t)v[4 * k + 1], (uint32_t)v[4 * k + 2],
+                                       (uint32_t)v[4 * k + 3]);
+    }
+}
+
 template <typename VT>
 __device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
     if constexpr (sizeof(VT) == 2) {
@@ -238,7 +291,7 @@ __device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
 template <typename VT, int kNegReset>
 __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArgs a, const __grid_constant__ CUtensorMap wmap) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full[4], s_empty[4], acc_full[2], acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full, s_free, acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
 
@@ -251,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = (int)((long long)blockIdx.x * a.items / gridDim.x);
     const int i1 = (int)((long long)(blockIdx.x + 1) * a.items / gridDim.x);
+    const int n_items = i1 - i0;
     const int r0 = (int)(a.tick & (kRows - 1));
 
     // 4 fp16 values (1.0 or 0.0) for every nibble of spike bits.  The table is
@@ -266,13 +320,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     if (tid == 0) {
         mbar_init(&bar_w, 1);
         mbar_init(&bar_drain, 1);
-        for (int k = 0; k < 4; ++k) {
-            mbar_init(&s_full[k], 2);
-            mbar_init(&s_empty[k], 1);
-        }
+        mbar_init(&s_full, kWorkers);
+        mbar_init(&s_free, 1);
         for (int k = 0; k < 2; ++k) {
             mbar_init(&acc_full[k], 1);
-            mbar_init(&acc_empty[k], kEpiWarps);
+            mbar_init(&acc_empty[k], kWorkers);
         }
         abort_sh = 0;
         fence_mbar_init();
@@ -291,180 +343,178 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         return false;
     };
 
-    if (warp < kEpiWarps) {
-        // ------------------------------------------------------------ epilogue
-        // Unit u = (neuron half h, 32-sample chunk cc); this warp owns units
-        // g*nu .. g*nu+nu-1 for TMEM lanes 32q..32q+31.  The potentials of the
-        // first kPre units are loaded before waiting for the accumulator and
-        // the rest are loaded kPre units ahead, so global latency overlaps
-        // the tensor-core work.
-        const int q = warp & 3, g = warp >> 2, nu = 2 * NH;
+    if (warp < kWorkers) {
+        // ------------------------------------------------------------ workers
+        // Iteration li: (1) build the operand tile S of item li (the tensor
+        // core is idle, waiting for it); (2) epilogue of item li-1 while the
+        // tensor core works on item li.
+        //
+        // Epilogue units: (neuron half h, 32-sample chunk cc).  Warp (q, g)
+        // owns TMEM lanes 32q..32q+31 and units of one neuron
+        // n = h*128 + 32q + lane: with two halves, h = g/2 and chunks
+        // 2(g%2), 2(g%2)+1; with one half, chunk g.
+        const int q = warp & 3, g = warp >> 2;
+        const int nu = NH == 2 ? 2 : 1;
+        const int h = NH == 2 ? (g >> 1) : 0;
+        const int cc0 = NH == 2 ? (g & 1) * 2 : g;
+        const int n = h * 128 + q * 32 + lane;
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
-        constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;
+        constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;      // units whose potentials are loaded early
         VT *Vg = reinterpret_cast<VT *>(a.V);
-        // Every unit of this warp is the same neuron (only the 32-sample chunk
-        // differs), so its parameters change only when the core does.
-        const int n = (NH == 2 ? g * 128 : 0) + q * 32 + lane;
-        int pc = -1;
+        // Build tasks: (axon block ab, sample word sw); warp w takes tasks w and w + 16.
+        const int ntask_all = (A / 32) * 4;
+        const int ntask = (warp < ntask_all ? 1 : 0) + (warp + kWorkers < ntask_all ? 1 : 0);
+        int pc = -1, bc = -1;
         int lam = 0, pth = 0, nth = 0, rst = 0;
         uint2 dd = make_uint2(0u, 0u);
-        for (int it = i0; it < i1; ++it) {
-            const int li = it - i0, c = it / T, j = it % T, buf = li & 1;
-            if (c != pc) {
-                const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
-                lam = pr.x - 0x4B400000;  // folds the fp32 -> int bias of f32_bits_minus_bias
-                pth = pr.y;
-                nth = pr.z;
-                rst = pr.w;
-                dd = a.dst[(size_t)c * N + n];
-                pc = c;
-            }
-            const uint32_t kind = dest_kind(dd);
+        uint32_t od[2] = {0u, 0u};
+        uint32_t wnext[2] = {0u, 0u};
+        auto task_ax = [&](int k) { return 32 * ((warp + kWorkers * k) >> 2) + lane; };
+        auto task_sw = [&](int k) { return (warp + kWorkers * k) & 3; };
+        auto load_words = [&](int it, uint32_t (&w)[2]) {
+            const int c = it / T, j = it % T;
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (k < ntask) w[k] = row[(size_t)task_ax(k) * 4 + task_sw(k)];
+        };
+        if (n_items > 0) load_words(i0, wnext);
+        for (int li = 0; li <= n_items; ++li) {
+            // Potentials of the epilogue item (li - 1), loaded before the build.
+            const int le = li - 1, ite = i0 + le;
+            const int ce = ite / T, je = ite % T;
             uint4 vb[kPre][kVecs];
             auto vaddr = [&](int k) {
-                const int cc = (g * nu + k) & 3;
-                return reinterpret_cast<uint4 *>(Vg + ((((size_t)j * C + c) * 4 + cc) * N + n) * 32);
+                return reinterpret_cast<uint4 *>(Vg + ((((size_t)je * C + ce) * 4 + cc0 + k) * N + n) * 32);
             };
+            if (le >= 0) {
 #pragma unroll
-            for (int k = 0; k < kPre; ++k)
-                if (k < nu) {
-                    const uint4 *vp = vaddr(k);
+                for (int k = 0; k < kPre; ++k)
+                    if (k < nu) {
+                        const uint4 *vp = vaddr(k);
 #pragma unroll
-                    for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e];
-                }
-            if (!wait(&acc_full[buf], (li >> 1) & 1)) break;
-            tc_fence_after();
-            uint32_t n_sp = 0, n_pk = 0, n_out = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (k >= nu) break;
-                __syncwarp();
-                const int u = g * nu + k, h = u >> 2, cc = u & 3;
-                int v[32];
-                unpack32<VT>(vb[k % kPre], v);
-                uint32_t d[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NH * 128 + h * 128 + cc * 32), d);
-                uint32_t mask = 0u;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
-                    const bool fire = x >= pth;
-                    int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
-                    y = fire ? rst : y;
-                    v[i] = y;
-                    mask |= (fire ? 1u : 0u) << i;
-                }
-                store32<VT>(reinterpret_cast<VT *>(vaddr(k)), v);
-                if (k + kPre < nu) {
-                    const uint4 *vp = vaddr(k + kPre);
-#pragma unroll
-                    for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e];
-                }
-                a.spk[(((size_t)j * C + c) * 4 + cc) * N + n] = mask;
-                const uint32_t valid = valid_mask(a.n_valid, j * 128 + cc * 32);
-                const uint32_t live = mask & valid;
-                n_sp += __popc(live);
-                if (mask) {
-                    if (kind == RANC_DEST_CORE) {
-                        const uint32_t ax = dest_axon(dd);
-                        const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
-                        atomicOr(reinterpret_cast<uint32_t *>(a.ring) +
-                                     ((((size_t)j * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
-                                 mask);
-                        n_pk += __popc(live);
-                    } else if (kind == RANC_DEST_OUTPUT) {
-                        for (uint32_t m = live; m; m &= m - 1u) {
-                            const int b = j * 128 + cc * 32 + __ffs(m) - 1;
-                            atomicAdd(a.out + (size_t)b * a.n_out + dd.x, 1u);
-                        }
-                        n_out += __popc(live);
+                        for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e];
                     }
-                }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            n_sp = __reduce_add_sync(0xffffffffu, n_sp);
-            n_pk = __reduce_add_sync(0xffffffffu, n_pk);
-            n_out = __reduce_add_sync(0xffffffffu, n_out);
-            if (lane == 0 && (n_sp | n_pk | n_out)) {
-                unsigned long long *cp = a.cnt + ((size_t)j * C + c) * 4;
-                atomicAdd(cp + 0, (unsigned long long)n_sp);
-                atomicAdd(cp + 1, (unsigned long long)n_pk);
-                atomicAdd(cp + 2, (unsigned long long)n_out);
-            }
-        }
-    } else if (warp < kMmaWarp) {
-        // ------------------------------------------------------------ producers
-        // Warp p builds K-blocks kb0 = p/2 and kb0 + 2 (axon block 2kb + p%2
-        // of each).  Input lines were already ORed into the scheduler rows
-        // (inject_inputs), so a row is the whole active-axon set of its tick.
-        // Rows are loaded into registers three items ahead of their use.
-        const int p = warp - kProdWarp0, kb0 = p >> 1;
-        const int ntask = (kb0 < KB ? 1 : 0) + (kb0 + 2 < KB ? 1 : 0);
-        int axn[2];
-        axn[0] = 32 * (2 * kb0 + (p & 1)) + lane;
-        axn[1] = 32 * (2 * (kb0 + 2) + (p & 1)) + lane;
-        uint4 R0[2], R1[2], R2[2];
-        auto rows = [&](int it, uint4 (&R)[2]) {
-            if (it >= i1) return;
-            const int c = it / T, j = it % T;
+            // ---- (1) build S of item li
+            if (li < n_items) {
+                const int it = i0 + li, c = it / T, j = it % T;
+                if (!wait(&s_free, (li & 1) ^ 1)) break;
+                if (c != bc) {
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
-                if (t < ntask) R[t] = a.ring[(((size_t)j * C + c) * kRows + r0) * A + axn[t]];
-        };
-        if (ntask > 0) {
-            rows(i0, R0);
-            rows(i0 + 1, R1);
-            rows(i0 + 2, R2);
-        }
-        for (int it = i0; it < i1 && ntask > 0; ++it) {
-            const int li = it - i0, c = it / T, j = it % T;
-            bool ok = true;
-            unsigned long long ev = 0;
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                if (t >= ntask) break;
-                const int kb = kb0 + 2 * t, ab = 2 * kb + (p & 1), ax = axn[t];
-                if (!wait(&s_empty[kb], (li & 1) ^ 1)) {
-                    ok = false;
-                    break;
+                    for (int k = 0; k < 2; ++k)
+                        if (k < ntask) od[k] = a.outdeg[(size_t)c * A + task_ax(k)];
+                    bc = c;
                 }
-                const uint4 Rt = R0[t];
-                a.ring[(((size_t)j * C + c) * kRows + r0) * A + ax] = make_uint4(0u, 0u, 0u, 0u);
-                const uint32_t od = a.outdeg[(size_t)c * A + ax];
-                ev += (unsigned long long)od * (__popc(Rt.x & valid_mask(a.n_valid, j * 128)) +
-                                                __popc(Rt.y & valid_mask(a.n_valid, j * 128 + 32)) +
-                                                __popc(Rt.z & valid_mask(a.n_valid, j * 128 + 64)) +
-                                                __popc(Rt.w & valid_mask(a.n_valid, j * 128 + 96)));
-                uint8_t *blk = Ssm + (size_t)kb * kBlockBytes;
-                const uint32_t words[4] = {Rt.x, Rt.y, Rt.z, Rt.w};
+                const uint32_t wcur[2] = {wnext[0], wnext[1]};
+                if (li + 1 < n_items) load_words(it + 1, wnext);
+                uint32_t *row = reinterpret_cast<uint32_t *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
+                unsigned long long ev = 0;
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const uint32_t y = transpose32(words[w], lane);
-                    const int row = 32 * w + lane;
+                for (int k = 0; k < 2; ++k) {
+                    if (k >= ntask) break;
+                    const int ax = task_ax(k), sw = task_sw(k), ab = ax >> 5;
+                    row[(size_t)ax * 4 + sw] = 0u;
+                    ev += (unsigned long long)od[k] * __popc(wcur[k] & valid_mask(a.n_valid, j * 128 + sw * 32));
+                    const uint32_t y = transpose32(wcur[k], lane);
+                    const int srow = 32 * sw + lane;
+                    uint8_t *blk = Ssm + (size_t)(ab >> 1) * kBlockBytes + srow * 128;
 #pragma unroll
                     for (int qq = 0; qq < 4; ++qq) {
                         const int chunk = (ab & 1) * 4 + qq;
                         const uint2 lo = lut[(y >> (8 * qq)) & 0xFu], hi = lut[(y >> (8 * qq + 4)) & 0xFu];
-                        *reinterpret_cast<uint4 *>(blk + row * 128 + ((chunk ^ (row & 7)) << 4)) =
-                            make_uint4(lo.x, lo.y, hi.x, hi.y);
+                        *reinterpret_cast<uint4 *>(blk + ((chunk ^ (srow & 7)) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
                     }
                 }
                 fence_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&s_full[kb]);
-            }
-            if (!ok) break;
+                if (lane == 0) mbar_arrive(&s_full);
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                R0[t] = R1[t];
-                R1[t] = R2[t];
+                for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+                if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
             }
-            rows(it + 3, R2);
+            // ---- (2) epilogue of item li - 1
+            if (le >= 0) {
+                const int buf = le & 1;
+                if (ce != pc) {
+                    const int4 pr = a.prm[(size_t)ce * N + n];  // leak, pos_thr, neg_thr, reset
+                    lam = pr.x - 0x4B400000;  // folds the bias of f32_bits_minus_bias
+                    pth = pr.y;
+                    nth = pr.z;
+                    rst = pr.w;
+                    dd = a.dst[(size_t)ce * N + n];
+                    pc = ce;
+                }
+                if (!wait(&acc_full[buf], (le >> 1) & 1)) break;
+                tc_fence_after();
+                const uint32_t kind = dest_kind(dd);
+                uint32_t n_sp = 0, n_pk = 0, n_out = 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-            if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
+                for (int k = 0; k < 2; ++k) {
+                    if (k >= nu) break;
+                    const int cc = cc0 + k;
+                    if (k >= kPre) {
+                        const uint4 *vp = vaddr(k);
+#pragma unroll
+                        for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e];
+                    }
+                    uint4 *vout = vaddr(k);
+                    uint32_t mask = 0u;
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        __syncwarp();
+                        uint32_t d[16];
+                        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NH * 128 + h * 128 + cc * 32 + hf * 16), d);
+                        int v[16];
+                        unpack16<VT>(vb[k % kPre], hf, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
+                            const bool fire = x >= pth;
+                            int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
+                            y = fire ? rst : y;
+                            v[i] = y;
+                            mask |= (fire ? 1u : 0u) << (hf * 16 + i);
+                        }
+                        store16<VT>(vout, hf, v);
+                    }
+                    a.spk[(((size_t)je * C + ce) * 4 + cc) * N + n] = mask;
+                    const uint32_t valid = valid_mask(a.n_valid, je * 128 + cc * 32);
+                    const uint32_t live = mask & valid;
+                    n_sp += __popc(live);
+                    if (mask && kind == RANC_DEST_CORE) {
+                        const uint32_t ax = dest_axon(dd);
+                        const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
+                        atomicOr(reinterpret_cast<uint32_t *>(a.ring) + ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
+                                 mask);
+                        n_pk += __popc(live);
+                    }
+                    // Output bus: one warp-wide pass per output neuron that fired;
+                    // lane i adds sample cc*32 + i, so no lane loops over spikes.
+                    uint32_t olanes = __ballot_sync(0xffffffffu, kind == RANC_DEST_OUTPUT && live != 0u);
+                    if (kind == RANC_DEST_OUTPUT) n_out += __popc(live);
+                    while (olanes) {
+                        const int L = __ffs(olanes) - 1;
+                        olanes &= olanes - 1u;
+                        const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
+                        const uint32_t idL = __shfl_sync(0xffffffffu, dd.x, L);
+                        if ((mL >> lane) & 1u)
+                            atomicAdd(a.out + (size_t)(je * 128 + cc * 32 + lane) * a.n_out + idL, 1u);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                n_sp = __reduce_add_sync(0xffffffffu, n_sp);
+                n_pk = __reduce_add_sync(0xffffffffu, n_pk);
+                n_out = __reduce_add_sync(0xffffffffu, n_out);
+                if (lane == 0 && (n_sp | n_pk | n_out)) {
+                    unsigned long long *cp = a.cnt + ((size_t)je * C + ce) * 4;
+                    atomicAdd(cp + 0, (unsigned long long)n_sp);
+                    atomicAdd(cp + 1, (unsigned long long)n_pk);
+                    atomicAdd(cp + 2, (unsigned long long)n_out);
+                }
+            }
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
@@ -481,9 +531,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     ++nd;
                 }
                 mbar_arrive_expect_tx(&bar_w, (uint32_t)N * A * 2);
-                for (int h = 0; h < NH; ++h)
+                for (int hh = 0; hh < NH; ++hh)
                     for (int kb = 0; kb < KB; ++kb)
-                        tma_load_3d(Wsm + (size_t)(h * KB + kb) * kBlockBytes, &wmap, kb * 64, h * 128, c, &bar_w);
+                        tma_load_3d(Wsm + (size_t)(hh * KB + kb) * kBlockBytes, &wmap, kb * 64, hh * 128, c, &bar_w);
                 w_pending = true;
                 if (!wait(&bar_w, nw & 1)) break;
                 w_pending = false;
@@ -499,26 +549,20 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 prefetch_l2(a.ring + (((size_t)j2 * C + c2) * kRows + r0) * A, (uint32_t)A * 16u);
             }
             if (!wait(&acc_empty[buf], ((li >> 1) & 1) ^ 1)) break;
+            if (!wait(&s_full, li & 1)) break;
             tc_fence_after();
-            bool ok = true;
             for (int kb = 0; kb < KB; ++kb) {
-                if (!wait(&s_full[kb], li & 1)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
 #pragma unroll 1
-                for (int h = 0; h < NH; ++h) {
-                    const uint32_t d = tmem + (uint32_t)(buf * NH * 128 + h * 128);
-                    const uint32_t wa = smem_u32(Wsm + (size_t)(h * KB + kb) * kBlockBytes);
+                for (int hh = 0; hh < NH; ++hh) {
+                    const uint32_t d = tmem + (uint32_t)(buf * NH * 128 + hh * 128);
+                    const uint32_t wa = smem_u32(Wsm + (size_t)(hh * KB + kb) * kBlockBytes);
                     const uint32_t sb = smem_u32(Ssm + (size_t)kb * kBlockBytes);
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
                         mma_f16(d, smem_desc(wa + ks * 32), smem_desc(sb + ks * 32), (kb | ks) != 0);
                 }
-                mma_commit(&s_empty[kb]);
             }
-            if (!ok) break;
+            mma_commit(&s_free);
             mma_commit(&acc_full[buf]);
         }
         // Drain: all MMAs issued by this thread complete before tensor memory is freed.
@@ -536,13 +580,19 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
 // Helper kernels: reset, input transposition, state export / import
 // ---------------------------------------------------------------------------
 
+// V <- v0: each run of 32 samples of one (tile, core, chunk, neuron) holds one
+// value, written as 16-byte vectors.
 template <typename VT>
-__global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long total) {
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total; f += (long long)gridDim.x * blockDim.x) {
-        const long long e = f / 32;  // ((j*C + c)*4 + cc)*N + n
-        const int n = (int)(e % N);
+__global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long runs) {
+    constexpr int kVecs = 32 * (int)sizeof(VT) / 16;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < runs; e += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(e % N);                 // e = ((j*C + c)*4 + cc)*N + n
         const int c = (int)((e / N / 4) % C);
-        V[f] = (VT)v0[(size_t)c * N + n];
+        const int x = v0[(size_t)c * N + n];
+        const uint32_t w = sizeof(VT) == 2 ? (((uint32_t)x & 0xFFFFu) * 0x10001u) : (uint32_t)x;
+        uint4 *p = reinterpret_cast<uint4 *>(V + e * 32);
+#pragma unroll
+        for (int k = 0; k < kVecs; ++k) p[k] = make_uint4(w, w, w, w);
     }
 }
 
@@ -851,7 +901,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
 }
 
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
-    const long long total = (long long)sim->T * sim->C * 4 * sim->N * 32;
+    const long long total = (long long)sim->T * sim->C * 4 * sim->N;  // 32-sample runs
     if (sim->v16)
         batched_reset_v<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int16_t *)sim->V, sim->v0, sim->C, sim->N, total);
     else
