@@ -208,10 +208,12 @@ int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, i
 int ranc_save_state(ranc_sim *sim, void *buf, size_t *n);
 int ranc_load_state(ranc_sim *sim, const void *buf, size_t n);
 
-/* Per-kernel timing of the tick kernels with CUDA events on the handle's
- * stream (off by default).  ranc_read_kernel_timing returns the summed
- * duration in milliseconds and the number of timed tick-kernel launches since
- * timing was enabled; synchronous. */
+/* Timing of the tick kernels with CUDA events on the handle's stream (off by
+ * default; the events bracket only the kernels that advance ticks).
+ * ranc_read_kernel_timing returns their summed duration in milliseconds and
+ * the number of ticks they advanced since timing was enabled (one per launch
+ * for per-tick kernels; a persistent launch of ranc_run_samples advances
+ * window x ceil(n_samples / batch) ticks); synchronous. */
 int ranc_set_kernel_timing(ranc_sim *sim, int32_t enable);
 int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
 

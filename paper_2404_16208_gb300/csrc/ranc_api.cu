@@ -27,6 +27,7 @@ cudaError_t dev_alloc(void **p, size_t bytes);
 
 namespace {
 
+constexpr int RANC_ENOTSUP = -100;  // internal: take another code path
 thread_local std::string g_create_error;
 thread_local long long g_alloc_budget = -1;  // < 0: no fault injection
 
@@ -154,7 +155,8 @@ bool validate(const ranc_desc *d, int batch, int path, std::vector<int> &core_at
 
 void free_all(ranc_sim *s) {
     void *ptrs[] = {s->xbarT, s->tmask, s->wnk, s->prm, s->dst, s->in_ptr, s->in_line, s->in_axon, s->v0,
-                    s->V, s->ring, s->spk, s->out, s->cnt, s->inputs, s->err, s->digest, s->stage};
+                    s->V, s->ring, s->spk, s->out, s->cnt, s->inputs, s->err, s->digest, s->stage,
+                    s->gbar, s->counts_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     batched_teardown(s);
@@ -201,9 +203,10 @@ int fold_timing(ranc_sim *sim) {
         float ms = 0.f;
         CUDA_OR_FAIL(sim, cudaEventElapsedTime(&ms, sim->ev_pool[i], sim->ev_pool[i + 1]));
         sim->timed_ms += ms;
-        sim->timed_launches++;
+        sim->timed_launches += sim->ev_ticks[i / 2];
     }
     sim->ev_used = 0;
+    sim->ev_ticks.clear();
     return RANC_OK;
 }
 
@@ -243,7 +246,10 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
         }
         sim->launches++;
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "tick kernel launch: %s", cudaGetErrorString(e));
-        if (sim->timing) CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+        if (sim->timing) {
+            CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+            sim->ev_ticks.push_back(1);
+        }
         sim->tick++;
         sim->ticks_total += (unsigned long long)sim->n_valid;
     }
@@ -482,7 +488,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
             dmalloc(&sim->ring, (size_t)batch * C * kRows * AW) != cudaSuccess ||
             dmalloc(&sim->spk, (size_t)batch * C * (N / 32)) != cudaSuccess ||
             dmalloc(&sim->out, (size_t)batch * d->n_outputs) != cudaSuccess ||
-            dmalloc(&sim->cnt, (size_t)batch * C * 4) != cudaSuccess)
+            dmalloc(&sim->cnt, (size_t)batch * C * 4) != cudaSuccess || dmalloc(&sim->gbar, 2) != cudaSuccess)
             return abort_create(RANC_ENOMEM, "device allocation of the state arrays failed");
         sim->cnt_len = (size_t)batch * C * 4;
         e = plain_setup_kernel_attrs(N, AW);
@@ -638,6 +644,83 @@ extern "C" int ranc_reset(ranc_sim *sim) {
     return sync_and_check(sim);
 }
 
+// All sample windows of ranc_run_samples in one cooperative launch of the
+// persistent plain kernel.  Returns RANC_ENOTSUP when its grid cannot be
+// resident at once (the caller then uses per-tick launches).
+static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window,
+                                  uint32_t *counts, int mem) {
+    WindowArgs w{};
+    w.G = std::min(kMaxWindowCores, std::max(1, 1024 / sim->N));
+    w.n_groups = (sim->C + w.G - 1) / w.G;
+    w.n_samples = n_samples;
+    w.t_in = t_in;
+    w.window = window;
+    w.v0 = sim->v0;
+    w.bar = sim->gbar;
+    const size_t in_words = (size_t)n_samples * t_in * sim->in_words;
+    const uint32_t *dev_in = inputs;
+    if (mem == RANC_MEM_HOST && in_words > 0) {
+        int rc = ensure_stage(sim, in_words);
+        if (rc) return rc;
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->stage, inputs, in_words * 4, cudaMemcpyHostToDevice, sim->stream));
+        dev_in = sim->stage;
+    }
+    uint32_t *dev_counts = counts;
+    const size_t cwords = (size_t)n_samples * sim->n_outputs;
+    if (mem == RANC_MEM_HOST) {
+        if (cwords > sim->counts_cap) {
+            CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+            if (sim->counts_dev) cudaFree(sim->counts_dev);
+            sim->counts_dev = nullptr;
+            sim->counts_cap = 0;
+            if (dmalloc(&sim->counts_dev, cwords) != cudaSuccess) return fail(sim, RANC_ENOMEM, "count buffer");
+            sim->counts_cap = cwords;
+        }
+        dev_counts = sim->counts_dev;
+    }
+    w.counts = dev_counts;
+    PlainArgs &a = w.p;
+    a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
+    a.B = sim->B; a.n_valid = sim->B; a.in_words = sim->in_words; a.in_ticks = t_in;
+    a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = 0;
+    a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+    a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
+    a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (sim->timing) {
+        if (sim->ev_used + 2 > 4096) {
+            int rc = fold_timing(sim);
+            if (rc) return rc;
+        }
+        e0 = next_event(sim);
+        e1 = next_event(sim);
+        if (!e0 || !e1) return fail(sim, RANC_ECUDA, "cudaEventCreate failed");
+        CUDA_OR_FAIL(sim, cudaEventRecord(e0, sim->stream));
+    }
+    cudaError_t e = launch_plain_windows(w, sim->stream);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        if (sim->timing) sim->ev_used -= 2;
+        return RANC_ENOTSUP;
+    }
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "persistent window kernel: %s", cudaGetErrorString(e));
+    if (sim->timing) {
+        CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+        sim->ev_ticks.push_back((long long)window * ((n_samples + sim->B - 1) / sim->B));
+    }
+    sim->launches++;
+    sim->tick = window;
+    sim->ticks_total += (unsigned long long)window * n_samples;
+    sim->in_override = nullptr;
+    sim->in_ticks = 0;
+    sim->n_valid = sim->B;
+    if (mem == RANC_MEM_HOST) {
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts, dev_counts, cwords * 4, cudaMemcpyDeviceToHost, sim->stream));
+        return sync_and_check(sim);
+    }
+    return RANC_OK;
+}
+
 extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in,
                                 int32_t window, uint32_t *counts, int32_t mem) {
     CHECK_LIVE(sim);
@@ -645,6 +728,11 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
         (n_samples > 0 && !counts) || (mem != RANC_MEM_HOST && mem != RANC_MEM_DEVICE))
         return fail(sim, RANC_EINVAL, "bad run_samples arguments");
     const size_t per = (size_t)t_in * sim->in_words;
+    if (n_samples == 0) return RANC_OK;
+    if (sim->path == RANC_PATH_PLAIN) {
+        int rc = run_windows_persistent(sim, inputs, n_samples, t_in, window, counts, mem);
+        if (rc != RANC_ENOTSUP) return rc;  // otherwise fall through to per-tick launches
+    }
     for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
         const int ns = std::min(sim->B, n_samples - s0);
         int rc = reset_state(sim, false);

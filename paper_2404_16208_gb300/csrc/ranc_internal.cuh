@@ -49,6 +49,17 @@ struct PlainArgs {
     int stall_test;              // test only: CTA (0, 0) waits on an mbarrier nothing arrives on
 };
 
+// Persistent plain path (ranc_run_samples): G cores per CTA, all windows in one launch.
+constexpr int kMaxWindowCores = 32;
+struct WindowArgs {
+    PlainArgs p;                 // p.inputs = [n_samples][t_in][in_words]
+    int G, n_groups;             // cores per CTA, CTAs per batch slot
+    int n_samples, t_in, window;
+    const int *v0;               // [C][N]
+    uint32_t *counts;            // [n_samples][n_out] (device)
+    unsigned *bar;               // [2] grid barrier: arrivals, generation
+};
+
 // Batched-path device layout (one tile = kTileS samples, sample-minor bits).
 struct BatchedArgs {
     int C, A, N, AW, T;          // cores, axons, neurons, A/32, number of sample tiles
@@ -102,6 +113,9 @@ struct ranc_sim {
     size_t stage_cap = 0;
     int *err = nullptr;
     unsigned long long *digest = nullptr;
+    unsigned *gbar = nullptr;            // plain: grid barrier of the persistent window kernel
+    uint32_t *counts_dev = nullptr;      // plain: device copy of run_samples counts (host mode)
+    size_t counts_cap = 0;
     int n_valid = 0;
 
     long long tick = 0;
@@ -111,6 +125,7 @@ struct ranc_sim {
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
+    std::vector<long long> ev_ticks;     // ticks advanced by the kernel between each event pair
     int ev_used = 0;
     double timed_ms = 0.0;
     long long timed_launches = 0;
@@ -132,6 +147,7 @@ namespace ranc {
 // Implemented in ranc_plain.cu
 cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s);
 cudaError_t plain_setup_kernel_attrs(int N, int AW);
+cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s);
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s);
 // Implemented in ranc_batched.cu

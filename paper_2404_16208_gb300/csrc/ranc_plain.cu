@@ -147,6 +147,240 @@ cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form of the plain path for ranc_run_samples: one cooperative
+// launch runs every sample window.  A CTA owns G cores of one batch slot (one
+// thread per neuron, G*N threads), keeps their crossbars in shared memory and
+// each neuron's potential, parameters and weights in registers for the whole
+// launch; ticks are separated by a grid barrier (bounded wait).  The tick body
+// is the one of plain_tick_kernel.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier over all CTAs of a cooperative launch.  bar[0] counts
+// arrivals, bar[1] is the generation.  Returns false if the wait gave up.
+__device__ bool grid_sync(unsigned *bar, unsigned nblocks, unsigned &gen, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        __threadfence();
+        const unsigned g = gen;
+        if (atomicAdd(&bar[0], 1u) + 1u == nblocks) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], g + 1u);
+        } else if (ld_acquire_u32(&bar[1]) == g) {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(&bar[1]) == g) {
+                if (global_ns() - t0 > kWaitLimitNs) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    ++gen;
+    return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs w) {
+    extern __shared__ __align__(128) uint32_t sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t red[kMaxWindowCores][4];
+    __shared__ int s_ok;
+    const PlainArgs &a = w.p;
+    const int G = w.G, N = a.N, AW = a.AW, K = a.K, C = a.C;
+    const int grp = blockIdx.x % w.n_groups, b = blockIdx.x / w.n_groups;
+    const int tid = threadIdx.x, cg = tid / N, n = tid % N, lane = tid & 31;
+    const int c_first = grp * G, ncores = min(G, C - c_first);
+    const int c = c_first + cg;
+    const bool has_core = cg < ncores;
+    uint32_t *xs = sm;                         // [ncores][N][AW]
+    uint32_t *tm = xs + (size_t)G * N * AW;    // [ncores][K][AW]
+    uint32_t *sb = tm + (size_t)G * K * AW;    // [ncores][AW] active axons of this tick
+    uint32_t *inb = sb + (size_t)G * AW;       // [t_in][in_words] inputs of this CTA's sample
+    const unsigned nblocks = gridDim.x;
+    unsigned gen = 0;
+
+    const uint32_t xbytes = (uint32_t)ncores * N * AW * 4u;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, xbytes);
+        bulk_g2s(xs, a.xbarT + (size_t)c_first * N * AW, xbytes, &bar);
+    }
+    for (int i = tid; i < ncores * K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c_first * K * AW + i];
+    int lam = 0, pth = 0, nth = 0, rst = 0, v0 = 0;
+    uint32_t wr[4] = {0u, 0u, 0u, 0u};
+    uint2 dd = make_uint2(0u, 0u);
+    if (has_core) {
+        const int4 pr = a.prm[(size_t)c * N + n];
+        lam = pr.x;
+        pth = pr.y;
+        nth = pr.z;
+        rst = pr.w;
+        const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
+        wr[0] = (uint32_t)wv.x;
+        wr[1] = (uint32_t)wv.y;
+        wr[2] = (uint32_t)wv.z;
+        wr[3] = (uint32_t)wv.w;
+        dd = a.dst[(size_t)c * N + n];
+        v0 = w.v0[(size_t)c * N + n];
+    }
+    if (tid < kMaxWindowCores * 4) red[tid / 4][tid % 4] = 0u;
+    __syncthreads();
+    const bool ok0 = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok0)) {
+        if (tid == 0) atomicExch(a.err, kErrTimeout);
+        mbar_wait_bounded(&bar, 0);
+        return;
+    }
+    const uint32_t kind = dest_kind(dd);
+    const int ipw = w.t_in * a.in_words;
+    const int ip0 = a.in_ptr[c_first], ip1 = a.in_ptr[c_first + ncores];
+    uint32_t n_sp = 0, n_pk = 0, n_ou = 0, n_syn = 0;
+    int V = v0;
+    const int n_windows = (w.n_samples + a.B - 1) / a.B;
+    for (int win = 0; win < n_windows; ++win) {
+        const int smp = win * a.B + b;
+        const bool valid = smp < w.n_samples;
+        // Window start (reading R7): V = v0, this CTA's scheduler rows and (group 0) output row cleared.
+        V = v0;
+        uint32_t *rows = a.ring + ((size_t)b * C + c_first) * kRows * AW;
+        for (int i = tid; i < ncores * kRows * AW; i += blockDim.x) __stcg(rows + i, 0u);
+        if (grp == 0)
+            for (int i = tid; i < a.n_out; i += blockDim.x) __stcg(a.out + (size_t)b * a.n_out + i, 0u);
+        for (int i = tid; i < ipw; i += blockDim.x) inb[i] = valid ? __ldg(a.inputs + (size_t)smp * ipw + i) : 0u;
+        if (!grid_sync(w.bar, nblocks, gen, &s_ok)) break;
+        bool stop = false;
+        for (int t = 0; t < w.window; ++t) {
+            const int r = t & (kRows - 1);
+            for (int i = tid; i < ncores * AW; i += blockDim.x) {
+                uint32_t *p = a.ring + (((size_t)b * C + c_first + i / AW) * kRows + r) * AW + i % AW;
+                sb[i] = __ldcg(p);
+                __stcg(p, 0u);
+            }
+            __syncthreads();
+            if (valid && t < w.t_in) {
+                const uint32_t *in = inb + (size_t)t * a.in_words;
+                for (int k = ip0 + tid; k < ip1; k += blockDim.x) {
+                    const int L = a.in_line[k];
+                    if ((in[L >> 5] >> (L & 31)) & 1u) {
+                        int kc = 0;
+                        while (kc + 1 < ncores && k >= a.in_ptr[c_first + kc + 1]) ++kc;
+                        const int ax = a.in_axon[k];
+                        atomicOr(&sb[kc * AW + (ax >> 5)], 1u << (ax & 31));
+                    }
+                }
+                __syncthreads();
+            }
+            bool fire = false;
+            if (has_core) {
+                const uint32_t *xr = xs + ((size_t)cg * N + n) * AW;
+                const uint32_t *sc = sb + cg * AW;
+                const uint32_t *tc = tm + (size_t)cg * K * AW;
+                uint32_t cntk[kMaxTypes];
+#pragma unroll
+                for (int k = 0; k < kMaxTypes; ++k) cntk[k] = 0u;
+                uint32_t syn = 0u;
+                for (int wd = 0; wd < AW; ++wd) {
+                    const uint32_t sw = sc[wd];
+                    if (sw == 0u) continue;
+                    const uint32_t x = sw & xr[wd];
+                    syn += __popc(x);
+#pragma unroll
+                    for (int k = 0; k < kMaxTypes; ++k)
+                        if (k < K) cntk[k] += __popc(x & tc[k * AW + wd]);
+                }
+                int dv = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxTypes; ++k)
+                    if (k < K) dv += (int)(int16_t)(wr[k >> 1] >> (16 * (k & 1))) * (int)cntk[k];
+                int x = V + dv + lam;
+                fire = x >= pth;
+                if (fire)
+                    x = rst;
+                else if (x < nth)
+                    x = a.neg_mode ? rst : nth;
+                V = x;
+                if (valid) {
+                    n_syn += syn;
+                    n_sp += fire ? 1u : 0u;
+                }
+                if (fire) {
+                    if (kind == RANC_DEST_CORE) {
+                        const uint32_t ax = dest_axon(dd);
+                        const int rr = (t + (int)dest_delay(dd)) & (kRows - 1);
+                        atomicOr(a.ring + (((size_t)b * C + dd.x) * kRows + rr) * AW + (ax >> 5), 1u << (ax & 31));
+                        if (valid) ++n_pk;
+                    } else if (kind == RANC_DEST_OUTPUT) {
+                        atomicAdd(a.out + (size_t)b * a.n_out + dd.x, 1u);
+                        if (valid) ++n_ou;
+                    }
+                }
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fire);
+            if (has_core && lane == 0) a.spk[((size_t)b * C + c) * a.NW + n / 32] = fm;
+            if (!grid_sync(w.bar, nblocks, gen, &s_ok)) {
+                stop = true;
+                break;
+            }
+        }
+        if (stop) break;
+        if (grp == 0 && valid)
+            for (int i = tid; i < a.n_out; i += blockDim.x)
+                w.counts[(size_t)smp * a.n_out + i] = __ldcg(a.out + (size_t)b * a.n_out + i);
+        if (!grid_sync(w.bar, nblocks, gen, &s_ok)) break;
+    }
+    if (!s_ok) {
+        if (tid == 0) atomicExch(a.err, kErrTimeout);
+        return;
+    }
+    if (has_core) a.V[((size_t)b * C + c) * N + n] = V;
+    // Counters: per core of this CTA, summed over its valid windows.
+    n_sp = __reduce_add_sync(0xffffffffu, n_sp);
+    n_pk = __reduce_add_sync(0xffffffffu, n_pk);
+    n_ou = __reduce_add_sync(0xffffffffu, n_ou);
+    n_syn = __reduce_add_sync(0xffffffffu, n_syn);
+    if (has_core && lane == 0) {
+        atomicAdd(&red[cg][0], n_sp);
+        atomicAdd(&red[cg][1], n_pk);
+        atomicAdd(&red[cg][2], n_ou);
+        atomicAdd(&red[cg][3], n_syn);
+    }
+    __syncthreads();
+    if (tid < ncores * 4) a.cnt[((size_t)b * C + c_first + tid / 4) * 4 + tid % 4] += red[tid / 4][tid % 4];
+}
+
+// Launches plain_window_kernel when its grid fits on the device at once (the
+// barrier needs every CTA resident); returns cudaErrorCooperativeLaunchTooLarge
+// otherwise, so the caller can use the per-tick launches instead.
+cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
+    const int threads = w.G * w.p.N;
+    const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + (size_t)w.G * w.p.AW +
+                         (size_t)w.t_in * w.p.in_words) * 4;
+    cudaError_t e = cudaFuncSetAttribute(plain_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plain_window_kernel, threads, smem)) != cudaSuccess)
+        return e;
+    const int grid = w.n_groups * w.p.B;
+    if ((long long)per_sm * n_sm < grid) return cudaErrorCooperativeLaunchTooLarge;
+    if ((e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+    void *args[] = {const_cast<WindowArgs *>(&w)};
+    return cudaLaunchCooperativeKernel((const void *)plain_window_kernel, dim3(grid), dim3(threads), args, smem, s);
+}
+
 // V <- v0 for every sample.
 __global__ void plain_reset_v_kernel(int *V, const int *v0, long long per_sample, long long total) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;

@@ -183,4 +183,9 @@ def test_kernel_timing_and_launch_count(ranc):
     ms, n = ranc.ranc_read_kernel_timing(sim.h)
     assert n == 10 and ms > 0
     assert ranc.ranc_launch_count(sim.h) - n0 == 10
+    # one persistent launch for 5 samples in windows of 9 ticks (3 windows of batch 2)
+    ranc.ranc_set_kernel_timing(sim.h, True)
+    sim.run_samples(W.rate_coded_inputs(1, 5, 8, 784, 0.15), 9)
+    ms, n = ranc.ranc_read_kernel_timing(sim.h)
+    assert n == 27 and ms > 0
     sim.close()
