@@ -252,6 +252,43 @@ def e2e_batched(ranc, torch, net, x, n_samples):
     return dict(value=n_samples / dt, h2d=int(xh.nbytes), d2h=int(ch.nbytes))
 
 
+def bench_truenorth(ranc, torch, steps, warmup):
+    """Table I's TrueNorth-sized grid (4096 cores of 256 x 256, no application,
+    500 ticks) on the plain path, batch 1: a step is reset + 500 ticks."""
+    import ranc_workloads as W
+    import oracle
+    net = W.truenorth_ref()
+    sim = ranc.Sim(net, 1, ranc.RANC_PATH_PLAIN)
+    for _ in range(warmup):
+        sim.reset()
+        sim.step(500)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        sim.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(500)
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    ranc.ranc_set_kernel_timing(sim.h, True)
+    sim.step(50)
+    kms, kn = ranc.ranc_read_kernel_timing(sim.h)
+    sim.close()
+    oracle.build()
+    thr = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.run(net, np.zeros((1, 0, 0), np.uint32), 2, n_threads=thr)
+    per_tick_cpu = (time.perf_counter() - t0) / 2
+    return {"metric": "TrueNorth-reference grid: seconds per 500-tick run (4096 cores 256x256, batch 1)",
+            "value": ms / steps / 1e3, "unit": "s", "higher_is_better": False, "steps": steps, "warmup": warmup,
+            "avg_tick_us": 1e3 * kms / max(kn, 1), "paper_context": {"serial_cpu_s": 8295, "gpu_speedup": 521,
+            "hardware": "EPYC 7552 one core vs V100S"},
+            "cpu_baseline": {"value": per_tick_cpu * 500, "unit": "s (extrapolated from 2 ticks)",
+                             "cores": 1, "kind": "oracle", "sample": "2 ticks of one sample"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +300,8 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth"],
+                    help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1")
     args = ap.parse_args()
     rank, ws, local = dist_env()
 
@@ -301,6 +340,11 @@ def main():
     from paper_2404_16208_gb300 import build_library
     build_library()
     from paper_2404_16208_gb300 import ranc
+
+    if args.workload == "truenorth":
+        if rank == 0:
+            print(json.dumps(bench_truenorth(ranc, torch, args.steps, args.warmup)))
+        return
 
     if ws > 1:
         import torch.distributed as dist

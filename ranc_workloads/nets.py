@@ -104,15 +104,20 @@ def make_net(name, grid_w, grid_h, core_xy, syn, axon_type, weight, leak, pos_th
     ``syn`` is the dense 0/1 crossbar [C, A, N]; ``fanout`` a list of
     (line, core, axon) triples.
     """
-    syn = np.asarray(syn, dtype=np.uint8)
-    C, A, N = syn.shape
+    if isinstance(syn, tuple) and syn[0] == "packed":  # ("packed", uint32 [C, A, N/32], N)
+        packed = np.ascontiguousarray(syn[1], dtype=np.uint32)
+        C, A, N = packed.shape[0], packed.shape[1], int(syn[2])
+    else:
+        syn = np.asarray(syn, dtype=np.uint8)
+        C, A, N = syn.shape
+        packed = pack_bits_lsb(syn)
     as32 = lambda x: np.array(np.broadcast_to(np.asarray(x, dtype=np.int32), (C, N)), dtype=np.int32)
     offs, icore, iaxon = fanout_csr(n_inputs, fanout)
     return Net(
         name=name, grid_w=int(grid_w), grid_h=int(grid_h), axons=int(A), neurons=int(N),
         n_types=int(weight.shape[1]), weight_bits=int(weight_bits), neg_mode=int(neg_mode),
         core_xy=np.ascontiguousarray(np.asarray(core_xy, dtype=np.int16).reshape(C, 2)),
-        crossbar=np.ascontiguousarray(pack_bits_lsb(syn)),
+        crossbar=packed,
         axon_type=np.ascontiguousarray(np.asarray(axon_type, dtype=np.uint8).reshape(C, A)),
         weight=np.ascontiguousarray(np.asarray(weight, dtype=np.int16)),
         leak=as32(leak), pos_thr=as32(pos_thr), neg_thr=as32(neg_thr), reset=as32(reset),
@@ -212,6 +217,41 @@ def mnist_512core(seed=0x5EED0512, **over):
     return make_net("mnist-512core", GW, 16, xy, syn, atype, w, leak, pthr, p["neg_thr"], p["reset"],
                     dest, 784, 10, fan, weight_bits=9,
                     meta=dict(seed=seed, t_in=16, window=24, p_in=0.15, layers=(L1, L2, L3), params=p))
+
+
+# ---------------------------------------------------------------------------
+# TrueNorth-sized reference grid with no application (Table I, Sec. IV).
+# ---------------------------------------------------------------------------
+
+def truenorth_ref(seed=0x5EED4096, grid=64, axons=256, neurons=256, density=0.3):
+    """grid x grid cores of axons x neurons, random crossbars, weights and
+    destinations, no input lines and non-positive leaks with positive
+    thresholds: every tick performs the full update of every core but no
+    neuron ever fires (the paper's scaling case with no mapped application).
+    Built with array operations so the 4096-core grid takes seconds."""
+    C, A, N, K = grid * grid, axons, neurons, 4
+    packed = np.zeros((C, A, N // 32), np.uint32)
+    step = 128
+    for c0 in range(0, C, step):  # same draws as one call over (C, A, N), without the 2 GB temporary
+        c1 = min(C, c0 + step)
+        packed[c0:c1] = pack_bits_lsb(rng.bernoulli(seed, S_XBAR, (c1 - c0, A, N), density, offset=c0 * A * N))
+    syn = ("packed", packed, N)
+    atype = rng.uniform_int(seed, S_TYPE, (C, A), 0, K - 1)
+    w = rng.uniform_int(seed, S_WEIGHT, (C, K, N), -255, 255)
+    leak = rng.uniform_int(seed, S_LEAK, (C, N), -3, 0)
+    pthr = rng.uniform_int(seed, S_POSTHR, (C, N), 64, 1024)
+    nthr = rng.uniform_int(seed, S_NEGTHR, (C, N), -1024, -64)
+    xy = np.stack([np.arange(C) % grid, np.arange(C) // grid], axis=1).astype(np.int16)
+    u = rng.uniform_int(seed, S_DEST, (C, N, 4), 0, 2**31 - 1)
+    dst = u[..., 0] % C
+    dest = empty_dest(C, N)
+    dest["dx"] = xy[dst, 0] - xy[:, None, 0]
+    dest["dy"] = xy[dst, 1] - xy[:, None, 1]
+    dest["axon"] = u[..., 1] % A
+    dest["delay"] = 1 + u[..., 2] % 15
+    dest["kind"] = KIND_CORE
+    return make_net("truenorth-ref", grid, grid, xy, syn, atype, w, leak, pthr, nthr, 0, dest, 0, 10, [],
+                    weight_bits=9, meta=dict(seed=seed, ticks=500))
 
 
 # ---------------------------------------------------------------------------
