@@ -300,8 +300,9 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth"],
-                    help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1")
+    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse"],
+                    help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1; "
+                         "dse: surrogate-ranked design-space exploration (512 training points, 20000 candidates)")
     args = ap.parse_args()
     rank, ws, local = dist_env()
 
@@ -344,6 +345,16 @@ def main():
     if args.workload == "truenorth":
         if rank == 0:
             print(json.dumps(bench_truenorth(ranc, torch, args.steps, args.warmup)))
+        return
+    if args.workload == "dse":
+        if rank == 0:
+            from paper_2404_16208_gb300 import dse
+            t0 = time.perf_counter()
+            rep = dse.explore(n_train=512, n_val=128, n_candidates=20000, top_k=64, seed=11, steps=2000,
+                              n_samples=256)
+            rep.update(metric="design-space exploration: true objective of the surrogate's top 64 vs 64 random "
+                              "(exact re-simulation)", wall_seconds=time.perf_counter() - t0)
+            print(json.dumps(rep))
         return
 
     if ws > 1:

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libranc.so")
-UNITS = ("ranc_api.cu", "ranc_plain.cu", "ranc_batched.cu")
+UNITS = ("ranc_api.cu", "ranc_plain.cu", "ranc_batched.cu", "ranc_mlp.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,7 +30,8 @@ def _cuda_lib_dir(nvcc):
 
 
 def _sources_mtime():
-    paths = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(ROOT, "include", "ranc.h"), __file__]
+    inc = os.path.join(ROOT, "include")
+    paths = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(inc, f) for f in os.listdir(inc)] + [__file__]
     return max(os.path.getmtime(p) for p in paths)
 
 

@@ -1,0 +1,162 @@
+"""Design-space exploration with a learned surrogate.
+
+Simulating every candidate RANC configuration exactly is what makes design
+sweeps take hours to weeks (Sec. I); here a small network predicts, from a
+configuration's parameters, two outcomes measured by the exact simulator:
+
+* spike traffic: packets delivered per sample, relative to the nominal design;
+* output agreement: the fraction of samples whose output-bus class (argmax of
+  the output counts, lowest id on ties) equals the nominal design's class.
+
+Flow: simulate a seeded training set of design points on the GPU (batched
+path), train the surrogate with the library's own kernels (include/ranc_mlp.h:
+bf16 weights, fp32 accumulation, Adam), score many seeded candidates with it,
+and simulate only the best-ranked ones exactly.  The exact simulator stays the
+judge: reported gains compare re-simulated results of the surrogate's choice
+with an equally sized random choice.  PyTorch only holds device buffers.
+"""
+
+import time
+
+import numpy as np
+
+from ranc_workloads import dse as D
+
+from . import ranc
+from .mlp import MLP
+
+TRAFFIC_WEIGHT = 0.2
+HIDDEN = (128, 128, 128)
+
+
+def argmax_lowest(counts):
+    return np.argmax(counts, axis=1)  # numpy returns the first maximum: the lowest id
+
+
+def objective(agreement, rel_traffic):
+    """Higher is better: agree with the nominal design while sending fewer packets."""
+    return agreement - TRAFFIC_WEIGHT * rel_traffic
+
+
+class Evaluator:
+    """Exact simulation of design points on fixed seeded inputs."""
+
+    def __init__(self, n_samples=256, window=32, seed=0x5EEDD5E):
+        self.master = D.Master(seed)
+        self.x = D.prototype_inputs(seed, n_samples, 16)
+        self.window = window
+        self.n = n_samples
+        counts, packets = self.simulate(D.NOMINAL)
+        self.ref_class = argmax_lowest(counts)
+        self.ref_packets = max(packets, 1.0)
+        self.sim_seconds = 0.0
+        self.n_sims = 0
+
+    def simulate(self, point):
+        net = D.build(self.master, point)
+        sim = ranc.Sim(net, self.n, ranc.RANC_PATH_BATCHED)
+        counts = sim.run_samples(self.x, self.window)
+        packets = float(sim.counters()[1]) / self.n
+        sim.close()
+        return counts, packets
+
+    def targets(self, points):
+        """[n, 2]: (agreement, relative traffic) per point."""
+        out = np.zeros((len(points), 2), np.float64)
+        t0 = time.perf_counter()
+        for k, p in enumerate(points):
+            counts, packets = self.simulate(p)
+            out[k, 0] = float(np.mean(argmax_lowest(counts) == self.ref_class))
+            out[k, 1] = packets / self.ref_packets
+        self.sim_seconds += time.perf_counter() - t0
+        self.n_sims += len(points)
+        return out
+
+
+def features(points):
+    return np.stack([p.features() for p in points]).astype(np.float32)
+
+
+class Surrogate:
+    def __init__(self, seed=1, max_batch=256):
+        self.mlp = MLP((D.N_FEATURES,) + HIDDEN + (2,), max_batch, seed=seed)
+        self.max_batch = max_batch
+        self.mu = np.zeros(2)
+        self.sd = np.ones(2)
+
+    def fit(self, X, Y, steps=3000, lr=2e-3, seed=2):
+        import torch
+        self.mu, self.sd = Y.mean(axis=0), Y.std(axis=0) + 1e-6
+        Yn = ((Y - self.mu) / self.sd).astype(np.float32)
+        dx = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        dy = torch.from_numpy(np.ascontiguousarray(Yn)).cuda()
+        g = np.random.default_rng(seed)
+        n = X.shape[0]
+        bs = min(self.max_batch, n)
+        losses = []
+        for s in range(steps):
+            idx = torch.from_numpy(g.choice(n, size=bs, replace=False)).cuda()
+            xb, yb = dx[idx].contiguous(), dy[idx].contiguous()
+            want = s % 100 == 0 or s == steps - 1
+            loss, _ = self.mlp.loss_backward(xb.data_ptr(), yb.data_ptr(), bs) if want else (None, None)
+            if not want:
+                self.mlp.loss_backward(xb.data_ptr(), yb.data_ptr(), bs)
+            else:
+                losses.append(loss)
+            self.mlp.adam_step(lr=lr * (0.1 ** (s / steps)))
+        torch.cuda.synchronize()
+        return losses
+
+    def predict(self, X):
+        import torch
+        out = np.zeros((X.shape[0], 2), np.float32)
+        for a in range(0, X.shape[0], self.max_batch):
+            xb = torch.from_numpy(np.ascontiguousarray(X[a:a + self.max_batch])).cuda()
+            yb = torch.zeros((xb.shape[0], 2), dtype=torch.float32, device="cuda")
+            self.mlp.forward(xb.data_ptr(), xb.shape[0], yb.data_ptr())
+            torch.cuda.synchronize()
+            out[a:a + xb.shape[0]] = yb.cpu().numpy()
+        return out * self.sd + self.mu
+
+
+def spearman(a, b):
+    from scipy.stats import spearmanr
+    return float(spearmanr(a, b).correlation)
+
+
+def explore(n_train=512, n_val=128, n_candidates=20000, top_k=64, seed=11, steps=3000, n_samples=256,
+            evaluator=None):
+    """Train on simulated points, rank candidates, re-simulate the top_k and
+    a random top_k; returns a report dict."""
+    ev = evaluator or Evaluator(n_samples=n_samples)
+    pts = D.sample_points(seed, n_train + n_val)
+    Y = ev.targets(pts)
+    X = features(pts)
+    sur = Surrogate()
+    t0 = time.perf_counter()
+    losses = sur.fit(X[:n_train], Y[:n_train], steps=steps)
+    train_s = time.perf_counter() - t0
+    Yv = sur.predict(X[n_train:])
+    mae = np.abs(Yv - Y[n_train:]).mean(axis=0)
+    rho_val = spearman(objective(Yv[:, 0], Yv[:, 1]), objective(Y[n_train:, 0], Y[n_train:, 1]))
+    cand = D.sample_points(seed + 1, n_candidates)
+    t0 = time.perf_counter()
+    pred = sur.predict(features(cand))
+    rank_s = time.perf_counter() - t0
+    score = objective(pred[:, 0], pred[:, 1])
+    top = np.argsort(-score, kind="stable")[:top_k]
+    rnd = np.random.default_rng(seed + 2).choice(n_candidates, size=top_k, replace=False)
+    Yt = ev.targets([cand[i] for i in top])
+    Yr = ev.targets([cand[i] for i in rnd])
+    true_top, true_rnd = objective(Yt[:, 0], Yt[:, 1]), objective(Yr[:, 0], Yr[:, 1])
+    return dict(
+        n_train=n_train, n_val=n_val, n_candidates=n_candidates, top_k=top_k, train_steps=steps,
+        final_train_loss=losses[-1], val_mae_agreement=float(mae[0]), val_mae_rel_traffic=float(mae[1]),
+        val_spearman_objective=rho_val,
+        top_true_objective_mean=float(true_top.mean()), random_true_objective_mean=float(true_rnd.mean()),
+        top_true_objective_best=float(true_top.max()), random_true_objective_best=float(true_rnd.max()),
+        gain_mean=float(true_top.mean() - true_rnd.mean()),
+        spearman_top_pred_vs_true=spearman(score[top], true_top),
+        sims=ev.n_sims, sim_seconds=ev.sim_seconds, seconds_per_sim=ev.sim_seconds / max(ev.n_sims, 1),
+        train_seconds=train_s, rank_seconds=rank_s,
+        exact_sims_saved=n_candidates - top_k)

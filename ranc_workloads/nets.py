@@ -112,7 +112,10 @@ def make_net(name, grid_w, grid_h, core_xy, syn, axon_type, weight, leak, pos_th
         C, A, N = syn.shape
         packed = pack_bits_lsb(syn)
     as32 = lambda x: np.array(np.broadcast_to(np.asarray(x, dtype=np.int32), (C, N)), dtype=np.int32)
-    offs, icore, iaxon = fanout_csr(n_inputs, fanout)
+    if isinstance(fanout, tuple) and fanout[0] == "csr":  # ("csr", offsets, core, axon), already grouped by line
+        offs, icore, iaxon = (np.ascontiguousarray(a, dtype=np.int32) for a in fanout[1:])
+    else:
+        offs, icore, iaxon = fanout_csr(n_inputs, fanout)
     return Net(
         name=name, grid_w=int(grid_w), grid_h=int(grid_h), axons=int(A), neurons=int(N),
         n_types=int(weight.shape[1]), weight_bits=int(weight_bits), neg_mode=int(neg_mode),

@@ -25,10 +25,19 @@ def ranc():
     return mod
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(ranc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_surrogate_header_is_exported(ranc):
+    mlp_header = os.path.join(ROOT, "include", "ranc_mlp.h")
+    lib = C.CDLL(ranc.LIB_PATH)
+    names = declared_functions(mlp_header)
+    assert names and all(hasattr(lib, n) for n in names)
+    from paper_2404_16208_gb300 import mlp
+    assert sorted(mlp.EXPORTED) == names
 
 
 def test_header_declares_the_boundary():
