@@ -10,24 +10,31 @@
 // integer below 2^22 in magnitude, so fp32 accumulation in tensor memory is
 // exact and the result equals the integer sum of the CPU definition.
 //
-// Roles inside one CTA (416 threads, one CTA per SM, persistent over items):
-//   warps 0-7   epilogue: tensor memory -> registers (tcgen05.ld), potential
-//               update (leak, thresholds, reset), spike masks over 32 samples
-//               per neuron, delivery with one atomicOr per (neuron, 32 samples)
+// Roles inside one CTA (544 threads, one CTA per SM, persistent over items):
+//   warps 0-15  workers.  Iteration i: (1) read and clear the scheduler row of
+//               tick t for item i and expand its bits to the fp16 0/1 operand
+//               S (sample-contiguous, 128-byte swizzled: a scheduler word is
+//               already 32 consecutive samples of one axon, so no transpose);
+//               (2) epilogue of item i-1 while the tensor core works on item
+//               i: tensor memory -> registers (tcgen05.ld), potential update
+//               (leak, thresholds, reset), spike masks over 32 samples per
+//               neuron, delivery with one atomicOr per (neuron, 32 samples)
 //               into the sample-minor scheduler rows, output-bus counts;
-//   warps 8-11  producers: read and clear the scheduler row of tick t, OR the
-//               input lines of tick t, transpose 32x32 bit blocks and expand
-//               bits to fp16 0/1 operand tiles in the 128-byte swizzled
-//               K-major layout the tensor core reads;
-//   warp 12     tensor-memory allocation, TMA loads of the folded weights of
+//   warp 16     tensor-memory allocation, TMA loads of the folded weights of
 //               the current core (cp.async.bulk.tensor, 128-byte swizzle),
+//               L2 prefetch of the next items' potentials and rows,
 //               tcgen05.mma issue and commit.
 // Every mbarrier wait is bounded (global timer); a timeout sets the device
 // error word and all roles leave their loops, drain the tensor core and free
 // tensor memory before the CTA exits.
 //
 // Layouts (T tiles of 128 samples; sample m of tile j is batch index 128j+m):
-//   V     [T][C][4][N][32]   potentials (int16 when the range allows, else int32)
+//   V     [T][C][4][N/32][P][32][E]  potentials (int16 when the range allows,
+//                                    else int32): for 32-sample chunk cc and
+//                                    neuron group n/32, piece p holds samples
+//                                    E*p .. E*p+E-1 of the 32 neurons side by
+//                                    side (E = 16 bytes / element size, P = 32 / E),
+//                                    so a warp's 16-byte accesses are contiguous
 //   ring  [T][C][16][A][4]   scheduler rows: word k of axon a holds samples 32k..32k+31
 //   spk   [T][C][4][N]       spike masks of the last tick (32 samples per word)
 //   inT   [T][ticks][Lpad][4] input lines, same sample-minor packing
@@ -48,7 +55,7 @@ namespace {
 constexpr int kWorkers = 16;                 // warps 0-15: operand build + epilogue
 constexpr int kMmaWarp = 16;                 // warp 16: TMEM, TMA, MMA issue
 constexpr int kThreads = (kWorkers + 1) * 32;
-constexpr uint32_t kBlockBytes = 128u * 128u;  // 128 rows x 64 fp16 = one swizzled K-block
+constexpr uint32_t kBlockBytes = 128u * 128u;  // one 64-axon K-block: 128 weight rows or 128 samples x 64 fp16
 
 struct TickArgs {
     int C, A, N, NH, KB, T, n_valid, Lpad, in_ticks, n_out, neg_mode, items;
@@ -85,19 +92,34 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// Shared-memory matrix descriptors, 128-byte swizzle, descriptor version 1.
+// Weights (A): K-major, rows of 64 fp16 along K, 8-row groups 1024 bytes apart
+// (stride byte offset; the leading byte offset is unused for this swizzle).
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1u << 16;             // leading byte offset (unused for this swizzle)
+    d |= (uint64_t)1u << 16;             // leading byte offset (unused)
     d |= (uint64_t)(1024u >> 4) << 32;   // stride byte offset
     d |= (uint64_t)1u << 46;             // version
     d |= (uint64_t)2u << 61;             // 128-byte swizzle
     return d;
 }
 
-// Instruction descriptor: D fp32, A and B fp16, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// Spike operand (B): MN-major, rows of 64 samples (128 bytes) per axon; the
+// 8-axon groups of one 64-sample half form 1024-byte swizzle atoms.  The two
+// sample halves are 1024 bytes apart (leading byte offset) and consecutive
+// 8-axon groups 2048 bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024u >> 4) << 16;   // leading byte offset
+    d |= (uint64_t)(2048u >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1u << 46;             // version
+    d |= (uint64_t)2u << 61;             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D fp32, A and B fp16, A K-major, B MN-major (bit 16),
+// M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 16) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
@@ -111,18 +133,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-
-__device__ __forceinline__ __attribute__((unused)) void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -170,56 +180,6 @@ __device__ __forceinline__ int f32_bits_minus_bias(uint32_t bits) {
     return __float_as_int(__uint_as_float(bits) + 12582912.0f);
 }
 
-template <typename VT>
-__device__ __forceinline__ void load32(const VT *p, int (&v)[32]) {
-    if constexpr (sizeof(VT) == 2) {
-        const uint4 *q = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint4 u = q[k];
-            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                v[8 * k + 2 * e] = (int)(int16_t)(w[e] & 0xFFFFu);
-                v[8 * k + 2 * e + 1] = (int)w[e] >> 16;
-            }
-        }
-    } else {
-        const int4 *q = reinterpret_cast<const int4 *>(p);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int4 u = q[k];
-            v[4 * k] = u.x;
-            v[4 * k + 1] = u.y;
-            v[4 * k + 2] = u.z;
-            v[4 * k + 3] = u.w;
-        }
-    }
-}
-
-template <typename VT, int kVecs>
-__device__ __forceinline__ void unpack32(const uint4 (&q)[kVecs], int (&v)[32]) {
-    if constexpr (sizeof(VT) == 2) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                v[8 * k + 2 * e] = (int)(int16_t)(w[e] & 0xFFFFu);
-                v[8 * k + 2 * e + 1] = (int)w[e] >> 16;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            v[4 * k] = (int)q[k].x;
-            v[4 * k + 1] = (int)q[k].y;
-            v[4 * k + 2] = (int)q[k].z;
-            v[4 * k + 3] = (int)q[k].w;
-        }
-    }
-}
-
 // Potentials hf*16 .. hf*16+15 of one 32-sample unit held as 16-byte vectors.
 template <typename VT, int kVecs>
 __device__ __forceinline__ void unpack16(const uint4 (&q)[kVecs], int hf, int (&v)[16]) {
@@ -246,6 +206,8 @@ __device__ __forceinline__ void unpack16(const uint4 (&q)[kVecs], int hf, int (&
     }
 }
 
+// Writes potentials hf*16 .. hf*16+15 of one 32-sample unit: vector k of the
+// unit sits 32 vectors (one per neuron of the warp) after vector k-1.
 template <typename VT>
 __device__ __forceinline__ void store16(uint4 *p, int hf, const int (&v)[16]) {
     if constexpr (sizeof(VT) == 2) {
@@ -255,33 +217,22 @@ __device__ __forceinline__ void store16(uint4 *p, int hf, const int (&v)[16]) {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
                 w[e] = ((uint32_t)v[8 * k + 2 * e] & 0xFFFFu) | ((uint32_t)v[8 * k + 2 * e + 1] << 16);
-            p[hf * 2 + k] = make_uint4(w[0], w[1], w[2], w[3]);
+            p[(hf * 2 + k) * 32] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            p[hf * 4 + k] = make_uint4((uint32_t)v[4 * k], (uint32_t)v[4 * k + 1], (uint32_t)v[4 * k + 2],
-                                       (uint32_t)v[4 * k + 3]);
+            p[(hf * 4 + k) * 32] = make_uint4((uint32_t)v[4 * k], (uint32_t)v[4 * k + 1], (uint32_t)v[4 * k + 2],
+                                              (uint32_t)v[4 * k + 3]);
     }
 }
 
+// Element offset of potential (tile j, core c, neuron n, sample 32*cc + i) in
+// the interleaved layout described at the top of this file.
 template <typename VT>
-__device__ __forceinline__ void store32(VT *p, const int (&v)[32]) {
-    if constexpr (sizeof(VT) == 2) {
-        uint4 *q = reinterpret_cast<uint4 *>(p);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t w[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                w[e] = ((uint32_t)v[8 * k + 2 * e] & 0xFFFFu) | ((uint32_t)v[8 * k + 2 * e + 1] << 16);
-            q[k] = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-    } else {
-        int4 *q = reinterpret_cast<int4 *>(p);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) q[k] = make_int4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-    }
+__device__ __forceinline__ size_t v_index(int j, int c, int cc, int n, int i, int C, int N) {
+    constexpr int E = 16 / (int)sizeof(VT);
+    return ((((size_t)j * C + c) * 4 + cc) * N + (n & ~31)) * 32 + (size_t)((i / E) * 32 + (n & 31)) * E + (i % E);
 }
 
 // ---------------------------------------------------------------------------
@@ -298,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NH = a.NH, KB = a.KB, C = a.C, A = a.A, N = a.N, T = a.T;
     uint8_t *Wsm = base;                                   // [NH][KB] blocks of 128 rows x 128 B
-    uint8_t *Ssm = Wsm + (size_t)NH * KB * kBlockBytes;    // [KB] blocks
+    uint8_t *Ssm = Wsm + (size_t)NH * KB * kBlockBytes;    // [KB] blocks of [8 groups][2 halves][8 axons][64 samples]
     uint2 *lut = reinterpret_cast<uint2 *>(Ssm + (size_t)KB * kBlockBytes);  // 16 x 8 B: one row of banks
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -361,31 +312,29 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
         constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;      // units whose potentials are loaded early
         VT *Vg = reinterpret_cast<VT *>(a.V);
-        // Build tasks: (axon block ab, sample word sw); warp w takes tasks w and w + 16.
-        const int ntask_all = (A / 32) * 4;
-        const int ntask = (warp < ntask_all ? 1 : 0) + (warp + kWorkers < ntask_all ? 1 : 0);
+        // Build task of this lane: axon rax, samples 64*rhf .. 64*rhf+63 (two
+        // scheduler words, read as one 8-byte vector: a warp reads 256
+        // contiguous bytes of the row).
+        const int tau = warp * 32 + lane;
+        const bool has_task = tau < 2 * A;
+        const int rax = tau >> 1, rhf = tau & 1;
         int pc = -1, bc = -1;
         int lam = 0, pth = 0, nth = 0, rst = 0;
         uint2 dd = make_uint2(0u, 0u);
-        uint32_t od[2] = {0u, 0u};
-        uint32_t wnext[2] = {0u, 0u};
-        auto task_ax = [&](int k) { return 32 * ((warp + kWorkers * k) >> 2) + lane; };
-        auto task_sw = [&](int k) { return (warp + kWorkers * k) & 3; };
-        auto load_words = [&](int it, uint32_t (&w)[2]) {
+        uint32_t odr = 0u;
+        auto load_words = [&](int it) -> uint2 {
             const int c = it / T, j = it % T;
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                if (k < ntask) w[k] = row[(size_t)task_ax(k) * 4 + task_sw(k)];
+            const uint2 *row = reinterpret_cast<const uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
+            return has_task ? row[rax * 2 + rhf] : make_uint2(0u, 0u);
         };
-        if (n_items > 0) load_words(i0, wnext);
+        uint2 wnext = n_items > 0 ? load_words(i0) : make_uint2(0u, 0u);
         for (int li = 0; li <= n_items; ++li) {
             // Potentials of the epilogue item (li - 1), loaded before the build.
             const int le = li - 1, ite = i0 + le;
             const int ce = ite / T, je = ite % T;
             uint4 vb[kPre][kVecs];
-            auto vaddr = [&](int k) {
-                return reinterpret_cast<uint4 *>(Vg + ((((size_t)je * C + ce) * 4 + cc0 + k) * N + n) * 32);
+            auto vaddr = [&](int k) {  // this lane's first 16-byte vector of unit k
+                return reinterpret_cast<uint4 *>(Vg + v_index<VT>(je, ce, cc0 + k, n & ~31, 0, C, N)) + lane;
             };
             if (le >= 0) {
 #pragma unroll
@@ -393,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     if (k < nu) {
                         const uint4 *vp = vaddr(k);
 #pragma unroll
-                        for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e];
+                        for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e * 32];
                     }
             }
             // ---- (1) build S of item li
@@ -401,29 +350,31 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 const int it = i0 + li, c = it / T, j = it % T;
                 if (!wait(&s_free, (li & 1) ^ 1)) break;
                 if (c != bc) {
-#pragma unroll
-                    for (int k = 0; k < 2; ++k)
-                        if (k < ntask) od[k] = a.outdeg[(size_t)c * A + task_ax(k)];
+                    if (has_task) odr = a.outdeg[(size_t)c * A + rax];
                     bc = c;
                 }
-                const uint32_t wcur[2] = {wnext[0], wnext[1]};
-                if (li + 1 < n_items) load_words(it + 1, wnext);
-                uint32_t *row = reinterpret_cast<uint32_t *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
+                const uint2 wcur = wnext;
+                if (li + 1 < n_items) wnext = load_words(it + 1);
                 unsigned long long ev = 0;
+                if (has_task) {
+                    uint2 *row = reinterpret_cast<uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
+                    row[rax * 2 + rhf] = make_uint2(0u, 0u);
+                    const int m0 = j * 128 + rhf * 64;
+                    ev = (unsigned long long)odr * (unsigned)(__popc(wcur.x & valid_mask(a.n_valid, m0)) +
+                                                               __popc(wcur.y & valid_mask(a.n_valid, m0 + 32)));
+                    // Row rax of the 64-sample half rhf: 8 chunks of 8 samples
+                    // (16 bytes), chunk position XOR the row within its 8-axon
+                    // group (128-byte swizzle).  The two halves write their
+                    // chunks in opposite order, so the 8 lanes of one store
+                    // phase hit 8 distinct bank groups.
+                    const int r8 = rax & 7;
+                    uint8_t *blk = Ssm + (size_t)(rax >> 6) * kBlockBytes + ((rax & 63) >> 3) * 2048 + rhf * 1024 + r8 * 128;
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (k >= ntask) break;
-                    const int ax = task_ax(k), sw = task_sw(k), ab = ax >> 5;
-                    row[(size_t)ax * 4 + sw] = 0u;
-                    ev += (unsigned long long)od[k] * __popc(wcur[k] & valid_mask(a.n_valid, j * 128 + sw * 32));
-                    const uint32_t y = transpose32(wcur[k], lane);
-                    const int srow = 32 * sw + lane;
-                    uint8_t *blk = Ssm + (size_t)(ab >> 1) * kBlockBytes + srow * 128;
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        const int chunk = (ab & 1) * 4 + qq;
-                        const uint2 lo = lut[(y >> (8 * qq)) & 0xFu], hi = lut[(y >> (8 * qq + 4)) & 0xFu];
-                        *reinterpret_cast<uint4 *>(blk + ((chunk ^ (srow & 7)) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
+                    for (int s8 = 0; s8 < 8; ++s8) {
+                        const int chunk = s8 ^ (rhf * 4);
+                        const uint32_t by = (chunk < 4 ? wcur.x : wcur.y) >> (8 * (chunk & 3));
+                        const uint2 lo = lut[by & 0xFu], hi = lut[(by >> 4) & 0xFu];
+                        *reinterpret_cast<uint4 *>(blk + ((chunk ^ r8) << 4)) = make_uint4(lo.x, lo.y, hi.x, hi.y);
                     }
                 }
                 fence_async_smem();
@@ -456,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     if (k >= kPre) {
                         const uint4 *vp = vaddr(k);
 #pragma unroll
-                        for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e];
+                        for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e * 32];
                     }
                     uint4 *vout = vaddr(k);
                     uint32_t mask = 0u;
@@ -558,8 +509,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     const uint32_t wa = smem_u32(Wsm + (size_t)(hh * KB + kb) * kBlockBytes);
                     const uint32_t sb = smem_u32(Ssm + (size_t)kb * kBlockBytes);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks)
-                        mma_f16(d, smem_desc(wa + ks * 32), smem_desc(sb + ks * 32), (kb | ks) != 0);
+                    for (int ks = 0; ks < 4; ++ks)  // K = 16: 32 bytes along a weight row, two 8-axon groups of S
+                        mma_f16(d, smem_desc_kmajor(wa + ks * 32), smem_desc_mn(sb + ks * 4096), (kb | ks) != 0);
                 }
             }
             mma_commit(&s_free);
@@ -580,19 +531,20 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
 // Helper kernels: reset, input transposition, state export / import
 // ---------------------------------------------------------------------------
 
-// V <- v0: each run of 32 samples of one (tile, core, chunk, neuron) holds one
-// value, written as 16-byte vectors.
+// V <- v0: every 16-byte vector holds samples of one (tile, core, neuron), so
+// it is v0 of that neuron repeated.  Vector e of the interleaved layout:
+// e = (((j*C + c)*4 + cc)*(N/32) + n/32)*P + p)*32 + n%32.
 template <typename VT>
-__global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long runs) {
-    constexpr int kVecs = 32 * (int)sizeof(VT) / 16;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < runs; e += (long long)gridDim.x * blockDim.x) {
-        const int n = (int)(e % N);                 // e = ((j*C + c)*4 + cc)*N + n
-        const int c = (int)((e / N / 4) % C);
+__global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long vecs) {
+    constexpr int P = 32 * (int)sizeof(VT) / 16;
+    uint4 *p = reinterpret_cast<uint4 *>(V);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vecs; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / (32 * P);  // ((j*C + c)*4 + cc)*(N/32) + n/32
+        const int n = (int)(g % (N / 32)) * 32 + (int)(e % 32);
+        const int c = (int)((g / (N / 32) / 4) % C);
         const int x = v0[(size_t)c * N + n];
         const uint32_t w = sizeof(VT) == 2 ? (((uint32_t)x & 0xFFFFu) * 0x10001u) : (uint32_t)x;
-        uint4 *p = reinterpret_cast<uint4 *>(V + e * 32);
-#pragma unroll
-        for (int k = 0; k < kVecs; ++k) p[k] = make_uint4(w, w, w, w);
+        p[e] = make_uint4(w, w, w, w);
     }
 }
 
@@ -654,7 +606,7 @@ __global__ void export_state(const VT *Vb, const uint32_t *spkb, const uint32_t 
         if (f < nv) {
             const int n = (int)(f % N), c = (int)((f / N) % C), b = b0 + (int)(f / N / C);
             const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
-            v[f] = (int)Vb[((((size_t)j * C + c) * 4 + cc) * N + n) * 32 + i];
+            v[f] = (int)Vb[v_index<VT>(j, c, cc, n, i, C, N)];
         } else if (f < nv + ns) {
             const long long g = f - nv;
             const int wn = (int)(g % (N / 32)), c = (int)((g / (N / 32)) % C), b = b0 + (int)(g / (N / 32) / C);
@@ -686,7 +638,7 @@ __global__ void import_state(VT *Vb, uint32_t *spkb, uint32_t *ringb, int B, int
         if (f < nv) {
             const int n = (int)(f % N), c = (int)((f / N) % C), b = (int)(f / N / C);
             const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
-            Vb[((((size_t)j * C + c) * 4 + cc) * N + n) * 32 + i] = (VT)v[f];
+            Vb[v_index<VT>(j, c, cc, n, i, C, N)] = (VT)v[f];
         } else if (f < nv + ns) {
             const long long g = f - nv;  // ((j*C + c)*4 + cc)*N + n
             const int n = (int)(g % N), cc = (int)((g / N) % 4), c = (int)((g / N / 4) % C), j = (int)(g / N / 4 / C);
@@ -901,7 +853,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
 }
 
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
-    const long long total = (long long)sim->T * sim->C * 4 * sim->N;  // 32-sample runs
+    const long long total = (long long)sim->T * sim->C * 4 * sim->N * (sim->v16 ? 4 : 8);  // 16-byte vectors
     if (sim->v16)
         batched_reset_v<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int16_t *)sim->V, sim->v0, sim->C, sim->N, total);
     else
