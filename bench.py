@@ -196,6 +196,12 @@ def plain_bytes_per_core_tick(net):
             + N // 8)           # spike bitmap
 
 
+POTENTIAL_DTYPE = {
+    0: "int32 potentials; fp16 0/1 and weight operands, fp32 accumulate (all exact)",
+    1: "int16 potentials; fp16 0/1 and weight operands, fp32 accumulate (all exact)",
+    2: "fp16 potentials (integers <= 2048, exact); fp16 0/1 and weight operands, fp32 accumulate (all exact)"}
+
+
 def batched_bytes_per_sample_core_tick(net, vbytes):
     """Algorithmic bytes per (sample, core, tick) of the batched tick kernel:
     the potential read and written once, the scheduler row read and cleared,
@@ -232,9 +238,10 @@ def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
     kms, kn = ranc.ranc_read_kernel_timing(sim.h)
     ranc.ranc_set_kernel_timing(sim.h, False)
     counts = dout.cpu().numpy()
+    fmt = sim.potential_format()
     sim.close()
     return dict(ms=ms, samples=n_samples * steps, events=int(cnt[3]), launches=launches, kernel_ms=kms,
-                kernel_launches=kn, counts=counts)
+                kernel_launches=kn, counts=counts, potential_format=fmt)
 
 
 def e2e_batched(ranc, torch, net, x, n_samples):
@@ -397,7 +404,8 @@ def main():
         return
 
     # Roofline of the dominant kernel (the batched tick kernel).
-    vbytes = 2  # int16 potentials: this workload's range [-1024, 2047] fits
+    fmt = br["potential_format"]
+    vbytes = 4 if fmt == ranc.RANC_POTENTIAL_INT32 else 2  # this workload's range [-1032, 2047] fits fp16
     kavg_ms = br["kernel_ms"] / max(br["kernel_launches"], 1)
     units = nb * net.n_cores
     bytes_launch = batched_bytes_per_sample_core_tick(net, vbytes) * units
@@ -431,7 +439,7 @@ def main():
     line = {
         "metric": METRIC, "value": samples_total / (ms_b * 1e-3), "unit": "samples/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32 (fp16 0/1 and weight operands, fp32 exact accumulate)",
+        "scaling": "weak", "vs_baseline": None, "dtype": POTENTIAL_DTYPE[fmt],
         "data": "synthetic",
         "synaptic_events_per_sec": br["events"] * ws / (ms_b * 1e-3),
         "config": {"workload": f"mnist-shaped 512-core net (256x256 cores), batched path, {nb} samples x "

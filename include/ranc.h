@@ -195,8 +195,9 @@ int ranc_reset(ranc_sim *sim);
  * samples, stepped `window` ticks, and its output-bus counts are written to
  * counts[s][n_outputs].  A last partial group leaves the unused samples
  * without input and without output.  `mem` says whether `inputs` and `counts`
- * are host (synchronous) or device (stream-ordered) memory.  Reading R7 of the
- * sample window: every sample starts from V = v0 and empty schedulers. */
+ * are host (synchronous) or device (stream-ordered) memory.  The paper streams
+ * images through one network (Table I) and says nothing of sample boundaries;
+ * here every sample starts from V = v0, empty schedulers and tick 0. */
 int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in, int32_t window,
                      uint32_t *counts, int32_t mem);
 
@@ -219,6 +220,24 @@ int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
 
 /* Number of kernels this handle has launched since ranc_create. */
 int ranc_launch_count(const ranc_sim *sim, int64_t *launches);
+
+/* How the handle stores the membrane potentials in device memory.  The paper
+ * makes the potential's bit width a configuration parameter (Sec. III and
+ * Sec. V); the library picks, at ranc_create, the narrowest storage that holds
+ * every value a neuron can take exactly (the paper gives no overflow rule; the
+ * potential is an integer that never wraps):
+ *   RANC_POTENTIAL_INT32  int32 (the plain path always; batched otherwise),
+ *   RANC_POTENTIAL_INT16  int16: every reachable value, i.e. v0, the reset
+ *                         value, theta- and the interval [theta-, theta+ - 1],
+ *                         lies in [-32768, 32767],
+ *   RANC_POTENTIAL_FP16   IEEE half precision: that range and the range plus
+ *                         the leak lie within +-2048, the leak and both
+ *                         thresholds lie within [-2047, 2048] (the batched
+ *                         tick is then computed on fp16 pairs, still exactly).
+ * The choice changes memory traffic only: results are identical in every
+ * format.  *format receives one of the values above. */
+enum { RANC_POTENTIAL_INT32 = 0, RANC_POTENTIAL_INT16 = 1, RANC_POTENTIAL_FP16 = 2 };
+int ranc_potential_format(const ranc_sim *sim, int32_t *format);
 
 /* Free every device and host resource of the handle.  NULL is a no-op. */
 void ranc_destroy(ranc_sim *sim);

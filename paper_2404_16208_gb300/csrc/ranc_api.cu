@@ -872,6 +872,14 @@ extern "C" int ranc_launch_count(const ranc_sim *sim, int64_t *launches) {
     return RANC_OK;
 }
 
+extern "C" int ranc_potential_format(const ranc_sim *sim, int32_t *format) {
+    if (!sim || !format) return RANC_EINVAL;
+    static_assert(RANC_POTENTIAL_INT32 == kVInt32 && RANC_POTENTIAL_INT16 == kVInt16 && RANC_POTENTIAL_FP16 == kVHalf,
+                  "storage codes");
+    *format = sim->path == RANC_PATH_PLAIN ? RANC_POTENTIAL_INT32 : sim->vmode;
+    return RANC_OK;
+}
+
 extern "C" void ranc_destroy(ranc_sim *sim) {
     if (!sim) return;
     cudaStreamSynchronize(sim->stream);

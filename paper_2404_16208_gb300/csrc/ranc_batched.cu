@@ -29,8 +29,9 @@
 // tensor memory before the CTA exits.
 //
 // Layouts (T tiles of 128 samples; sample m of tile j is batch index 128j+m):
-//   V     [T][C][4][N/32][P][32][E]  potentials (int16 when the range allows,
-//                                    else int32): for 32-sample chunk cc and
+//   V     [T][C][4][N/32][P][32][E]  potentials (fp16, int16 or int32, the
+//                                    narrowest that is exact for the network):
+//                                    for 32-sample chunk cc and
 //                                    neuron group n/32, piece p holds samples
 //                                    E*p .. E*p+E-1 of the 32 neurons side by
 //                                    side (E = 16 bytes / element size, P = 32 / E),
@@ -44,6 +45,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ranc_internal.cuh"
@@ -227,6 +229,18 @@ __device__ __forceinline__ void store16(uint4 *p, int hf, const int (&v)[16]) {
     }
 }
 
+// Potential storage: integer value <-> stored element.
+template <typename VT>
+__device__ __forceinline__ VT v_from_int(int x) {
+    if constexpr (std::is_same<VT, __half>::value) return __int2half_rn(x);
+    else return (VT)x;
+}
+template <typename VT>
+__device__ __forceinline__ int v_to_int(VT x) {
+    if constexpr (std::is_same<VT, __half>::value) return __half2int_rn(x);
+    else return (int)x;
+}
+
 // Element offset of potential (tile j, core c, neuron n, sample 32*cc + i) in
 // the interleaved layout described at the top of this file.
 template <typename VT>
@@ -311,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         const int n = h * 128 + q * 32 + lane;
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
         constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;      // units whose potentials are loaded early
+        constexpr bool kHalf = std::is_same<VT, __half>::value;
         VT *Vg = reinterpret_cast<VT *>(a.V);
         // Build task of this lane: axon rax, samples 64*rhf .. 64*rhf+63 (two
         // scheduler words, read as one 8-byte vector: a warp reads 256
@@ -322,6 +337,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         int lam = 0, pth = 0, nth = 0, rst = 0;
         uint2 dd = make_uint2(0u, 0u);
         uint32_t odr = 0u;
+        __half2 lam2 = __float2half2_rn(0.f), pth2 = lam2, nth2 = lam2;  // fp16 potentials only
+        uint32_t rst2 = 0u;
         auto load_words = [&](int it) -> uint2 {
             const int c = it / T, j = it % T;
             const uint2 *row = reinterpret_cast<const uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
@@ -393,6 +410,13 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     pth = pr.y;
                     nth = pr.z;
                     rst = pr.w;
+                    if constexpr (kHalf) {  // every one of these is an integer of magnitude <= 2048: exact
+                        lam2 = __float2half2_rn((float)pr.x);
+                        pth2 = __float2half2_rn((float)pr.y);
+                        nth2 = __float2half2_rn((float)pr.z);
+                        const __half2 r2 = __float2half2_rn((float)pr.w);
+                        rst2 = *reinterpret_cast<const uint32_t *>(&r2);
+                    }
                     dd = a.dst[(size_t)ce * N + n];
                     pc = ce;
                 }
@@ -416,18 +440,58 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                         __syncwarp();
                         uint32_t d[16];
                         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NH * 128 + h * 128 + cc * 32 + hf * 16), d);
-                        int v[16];
-                        unpack16<VT>(vb[k % kPre], hf, v);
+                        if constexpr (kHalf) {
+                            // Pairs of samples.  V + leak is exact in fp16, the
+                            // sum with dV exact in fp32; rounding that sum to
+                            // fp16 is monotone and keeps every integer of
+                            // magnitude <= 2048, so with both thresholds and
+                            // their predecessors representable the comparisons
+                            // decide as on the integers, and a value that is kept
+                            // (theta- <= x < theta+) is exact.  Overflow to
+                            // +-inf compares the same way.
+                            uint32_t wv[8];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
-                            const bool fire = x >= pth;
-                            int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
-                            y = fire ? rst : y;
-                            v[i] = y;
-                            mask |= (fire ? 1u : 0u) << (hf * 16 + i);
+                            for (int q2 = 0; q2 < 2; ++q2) {
+                                const uint4 u = vb[k % kPre][hf * 2 + q2];
+                                wv[4 * q2] = u.x;
+                                wv[4 * q2 + 1] = u.y;
+                                wv[4 * q2 + 2] = u.z;
+                                wv[4 * q2 + 3] = u.w;
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const float2 vl = __half22float2(__hadd2(*reinterpret_cast<const __half2 *>(&wv[e]), lam2));
+                                const __half2 x2 = __floats2half2_rn(__uint_as_float(d[2 * e]) + vl.x,
+                                                                     __uint_as_float(d[2 * e + 1]) + vl.y);
+                                const uint32_t fm = __hge2_mask(x2, pth2);
+                                uint32_t keep;
+                                if constexpr (kNegReset) {
+                                    const uint32_t rm = fm | __hlt2_mask(x2, nth2);
+                                    keep = *reinterpret_cast<const uint32_t *>(&x2);
+                                    wv[e] = (rm & rst2) | (~rm & keep);
+                                } else {
+                                    const __half2 c2 = __hmax2(x2, nth2);
+                                    keep = *reinterpret_cast<const uint32_t *>(&c2);
+                                    wv[e] = (fm & rst2) | (~fm & keep);
+                                }
+                                mask |= ((fm & 1u) | ((fm >> 15) & 2u)) << (hf * 16 + 2 * e);
+                            }
+                            vout[(hf * 2) * 32] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                            vout[(hf * 2 + 1) * 32] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+                        } else {
+                            int v[16];
+                            unpack16<VT>(vb[k % kPre], hf, v);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
+                                const bool fire = x >= pth;
+                                int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
+                                y = fire ? rst : y;
+                                v[i] = y;
+                                mask |= (fire ? 1u : 0u) << (hf * 16 + i);
+                            }
+                            store16<VT>(vout, hf, v);
                         }
-                        store16<VT>(vout, hf, v);
                     }
                     a.spk[(((size_t)je * C + ce) * 4 + cc) * N + n] = mask;
                     const uint32_t valid = valid_mask(a.n_valid, je * 128 + cc * 32);
@@ -542,8 +606,10 @@ __global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long ve
         const long long g = e / (32 * P);  // ((j*C + c)*4 + cc)*(N/32) + n/32
         const int n = (int)(g % (N / 32)) * 32 + (int)(e % 32);
         const int c = (int)((g / (N / 32) / 4) % C);
-        const int x = v0[(size_t)c * N + n];
-        const uint32_t w = sizeof(VT) == 2 ? (((uint32_t)x & 0xFFFFu) * 0x10001u) : (uint32_t)x;
+        const VT x = v_from_int<VT>(v0[(size_t)c * N + n]);
+        uint32_t w;
+        if constexpr (sizeof(VT) == 2) w = (uint32_t)(*reinterpret_cast<const uint16_t *>(&x)) * 0x10001u;
+        else w = (uint32_t)x;
         p[e] = make_uint4(w, w, w, w);
     }
 }
@@ -606,7 +672,7 @@ __global__ void export_state(const VT *Vb, const uint32_t *spkb, const uint32_t 
         if (f < nv) {
             const int n = (int)(f % N), c = (int)((f / N) % C), b = b0 + (int)(f / N / C);
             const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
-            v[f] = (int)Vb[v_index<VT>(j, c, cc, n, i, C, N)];
+            v[f] = v_to_int<VT>(Vb[v_index<VT>(j, c, cc, n, i, C, N)]);
         } else if (f < nv + ns) {
             const long long g = f - nv;
             const int wn = (int)(g % (N / 32)), c = (int)((g / (N / 32)) % C), b = b0 + (int)(g / (N / 32) / C);
@@ -638,7 +704,7 @@ __global__ void import_state(VT *Vb, uint32_t *spkb, uint32_t *ringb, int B, int
         if (f < nv) {
             const int n = (int)(f % N), c = (int)((f / N) % C), b = (int)(f / N / C);
             const int j = b >> 7, cc = (b & 127) >> 5, i = b & 31;
-            Vb[v_index<VT>(j, c, cc, n, i, C, N)] = (VT)v[f];
+            Vb[v_index<VT>(j, c, cc, n, i, C, N)] = v_from_int<VT>(v[f]);
         } else if (f < nv + ns) {
             const long long g = f - nv;  // ((j*C + c)*4 + cc)*N + n
             const int n = (int)(g % N), cc = (int)((g / N) % 4), c = (int)((g / N / 4) % C), j = (int)(g / N / 4 / C);
@@ -722,14 +788,24 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     sim->T = (sim->B + kTileS - 1) / kTileS;
     sim->B_pad = sim->T * kTileS;
 
-    // Potentials fit int16 when every value a neuron can hold does.
-    bool v16 = true;
+    // Storage of the potentials.  After a tick a neuron holds v0 (before its
+    // first tick), its reset value, theta-, or a value x with theta- <= x <
+    // theta+, so every stored value lies in [lo, hi] below.  int16 holds that
+    // range exactly when it fits.  fp16 is exact for the update (the tick
+    // kernel's fp16 branch) when [lo, hi] and [lo, hi] + leak lie within
+    // +-2048 (every integer there is an fp16 value) and theta+, theta+ - 1,
+    // theta-, theta- - 1 and the leak are representable.
+    bool fits16 = true, fitsh = true;
     for (size_t i = 0; i < (size_t)C * N; i++) {
-        const long long hi = std::max({(long long)d->pos_thr[i] - 1, (long long)d->reset[i], (long long)d->v0[i]});
-        const long long lo = std::min({(long long)d->neg_thr[i], (long long)d->reset[i], (long long)d->v0[i]});
-        if (hi > 32767 || lo < -32768) v16 = false;
+        const long long pt = d->pos_thr[i], nt = d->neg_thr[i], r = d->reset[i], v0 = d->v0[i], lk = d->leak[i];
+        const long long hi = std::max({pt - 1, nt, r, v0});
+        const long long lo = std::min({nt, r, v0});
+        if (hi > 32767 || lo < -32768) fits16 = false;
+        if (lo < -2048 || hi > 2048 || lo + lk < -2048 || hi + lk > 2048 || lk < -2048 || lk > 2048 || pt < -2047 ||
+            pt > 2048 || nt < -2047 || nt > 2048)
+            fitsh = false;
     }
-    sim->v16 = v16 ? 1 : 0;
+    sim->vmode = fitsh ? kVHalf : fits16 ? kVInt16 : kVInt32;
 
     // Folded weights W[c][n][a] = connected(a, n) ? w[type(a)][n] : 0 (fp16, exact).
     std::vector<__half> wf((size_t)C * N * A);
@@ -781,7 +857,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     }
     bs->n_pairs = (int)inj_ca.size();
     if (inj_ca.empty()) inj_ca.push_back(0);
-    const size_t vsz = v16 ? 2 : 4;
+    const size_t vsz = sim->vmode == kVInt32 ? 4 : 2;
     if (dev_alloc((void **)&bs->wfold, wf.size() * 2) != cudaSuccess || dev_alloc((void **)&bs->outdeg, od.size() * 2) != cudaSuccess ||
         dev_alloc((void **)&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
         dev_alloc((void **)&bs->fin_line, fline.size() * 4) != cudaSuccess ||
@@ -828,7 +904,9 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     }
     const int sm = (int)bs->smem;
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 0>, at, sm)) != cudaSuccess ||
+    if ((e = cudaFuncSetAttribute(batched_tick_kernel<__half, 0>, at, sm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(batched_tick_kernel<__half, 1>, at, sm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 0>, at, sm)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 1>, at, sm)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(batched_tick_kernel<int, 0>, at, sm)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(batched_tick_kernel<int, 1>, at, sm)) != cudaSuccess)
@@ -846,15 +924,18 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.inT = bs->inT; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
     a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
     const int grid = std::min(bs->n_sm, a.items);
-    auto kern = sim->v16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
-                         : (sim->neg_mode ? batched_tick_kernel<int, 1> : batched_tick_kernel<int, 0>);
+    auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
+                : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
+                                        : (sim->neg_mode ? batched_tick_kernel<int, 1> : batched_tick_kernel<int, 0>);
     kern<<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
-    const long long total = (long long)sim->T * sim->C * 4 * sim->N * (sim->v16 ? 4 : 8);  // 16-byte vectors
-    if (sim->v16)
+    const long long total = (long long)sim->T * sim->C * 4 * sim->N * (sim->vmode == kVInt32 ? 8 : 4);  // 16-byte vectors
+    if (sim->vmode == kVHalf)
+        batched_reset_v<__half><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((__half *)sim->V, sim->v0, sim->C, sim->N, total);
+    else if (sim->vmode == kVInt16)
         batched_reset_v<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int16_t *)sim->V, sim->v0, sim->C, sim->N, total);
     else
         batched_reset_v<int><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((int *)sim->V, sim->v0, sim->C, sim->N, total);
@@ -903,7 +984,10 @@ cudaError_t batched_inject(ranc_sim *sim) {
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk, uint32_t *ring) {
     const long long total = (long long)nb * sim->C * sim->N + (long long)nb * sim->C * (sim->N / 32) +
                             (ring ? (long long)nb * sim->C * kRows * (sim->A / 32) : 0);
-    if (sim->v16)
+    if (sim->vmode == kVHalf)
+        export_state<__half><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (const __half *)sim->V, sim->spk, sim->ring, b0, nb, sim->C, sim->N, sim->A, v, spk, ring);
+    else if (sim->vmode == kVInt16)
         export_state<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
             (const int16_t *)sim->V, sim->spk, sim->ring, b0, nb, sim->C, sim->N, sim->A, v, spk, ring);
     else
@@ -916,7 +1000,10 @@ cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *spk, const uint32_t *ring) {
     const long long total = (long long)sim->B * sim->C * sim->N + (long long)sim->T * sim->C * 4 * sim->N +
                             (long long)sim->T * sim->C * kRows * sim->A * 4;
-    if (sim->v16)
+    if (sim->vmode == kVHalf)
+        import_state<__half><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
+            (__half *)sim->V, sim->spk, sim->ring, sim->B, sim->T, sim->C, sim->N, sim->A, v, spk, ring);
+    else if (sim->vmode == kVInt16)
         import_state<int16_t><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
             (int16_t *)sim->V, sim->spk, sim->ring, sim->B, sim->T, sim->C, sim->N, sim->A, v, spk, ring);
     else

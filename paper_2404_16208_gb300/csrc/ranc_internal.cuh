@@ -15,6 +15,8 @@ constexpr int kRows = RANC_ROWS;     // scheduler rows (Sec. III-E); delays 1..1
 constexpr int kMaxTypes = 8;         // weight slots per neuron
 constexpr int kMaxWords = 32;        // axons/32 and neurons/32 upper bound (1024)
 constexpr int kTileS = 128;          // samples per tensor-core tile (batched path)
+// Storage of the batched path's potentials (values of RANC_POTENTIAL_*).
+constexpr int kVInt32 = 0, kVInt16 = 1, kVHalf = 2;
 constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // static scratch of the allocation-free read
 
 // Device error word values (set by kernels, read by synchronous host calls).
@@ -86,7 +88,7 @@ struct ranc_sim {
     // shape
     int C = 0, A = 0, N = 0, K = 0, B = 0, path = 0, neg_mode = 0;
     int grid_w = 0, grid_h = 0, n_inputs = 0, n_outputs = 0, in_words = 0, weight_bits = 0;
-    int B_pad = 0, T = 0, v16 = 0;      // batched path: padded batch, tiles, int16 potentials
+    int B_pad = 0, T = 0, vmode = 0;    // batched path: padded batch, tiles, potential storage (kVInt32 ...)
     cudaStream_t stream = nullptr;
     int device = 0;
 

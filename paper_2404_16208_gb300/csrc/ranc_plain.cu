@@ -252,7 +252,8 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     for (int win = 0; win < n_windows; ++win) {
         const int smp = win * a.B + b;
         const bool valid = smp < w.n_samples;
-        // Window start (reading R7): V = v0, this CTA's scheduler rows and (group 0) output row cleared.
+        // Window start (every sample starts from V = v0 and empty rows): V = v0, this CTA's scheduler rows and
+        // (group 0) output row cleared.
         V = v0;
         uint32_t *rows = a.ring + ((size_t)b * C + c_first) * kRows * AW;
         for (int i = tid; i < ncores * kRows * AW; i += blockDim.x) __stcg(rows + i, 0u);

@@ -23,7 +23,9 @@ EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
-            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_destroy", "ranc_last_error")
+            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_potential_format", "ranc_destroy",
+            "ranc_last_error")
+RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
 
 
 class RancError(RuntimeError):
@@ -70,6 +72,7 @@ def load_library(path=LIB_PATH):
         "ranc_set_kernel_timing": ([vp, i32], C.c_int),
         "ranc_read_kernel_timing": ([vp, C.POINTER(C.c_double), C.POINTER(i64)], C.c_int),
         "ranc_launch_count": ([vp, C.POINTER(i64)], C.c_int),
+        "ranc_potential_format": ([vp, C.POINTER(i32)], C.c_int),
         "ranc_destroy": ([vp], None),
         "ranc_last_error": ([vp], C.c_char_p),
     }
@@ -218,6 +221,12 @@ def ranc_launch_count(h):
     return n.value
 
 
+def ranc_potential_format(h):
+    f = C.c_int32()
+    _check(_lib.ranc_potential_format(h, C.byref(f)), h)
+    return f.value
+
+
 def ranc_destroy(h):
     _lib.ranc_destroy(h)
 
@@ -262,6 +271,10 @@ class Sim:
         counts = np.zeros((inputs.shape[0], self.net.n_outputs), np.uint32)
         ranc_run_samples(self.h, inputs, inputs.shape[0], inputs.shape[1], window, counts)
         return counts
+
+    def potential_format(self):
+        """RANC_POTENTIAL_INT32, _INT16 or _FP16: how the potentials are stored."""
+        return ranc_potential_format(self.h)
 
     def save(self):
         return ranc_save_state(self.h)

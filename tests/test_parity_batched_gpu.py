@@ -23,10 +23,28 @@ def ranc():
     return mod
 
 
-def per_tick_parity(ranc, oracle_mod, net, x, T):
+def expected_format(ranc, net):
+    """The storage the header promises: the reachable range [lo, hi] of every
+    neuron decides between fp16, int16 and int32."""
+    pt, nt = net.pos_thr.astype(np.int64), net.neg_thr.astype(np.int64)
+    r, v0, lk = net.reset.astype(np.int64), net.v0.astype(np.int64), net.leak.astype(np.int64)
+    hi = np.maximum.reduce([pt - 1, nt, r, v0])
+    lo = np.minimum.reduce([nt, r, v0])
+    half = (lo >= -2048) & (hi <= 2048) & (lo + lk >= -2048) & (hi + lk <= 2048) & (np.abs(lk) <= 2048) & \
+        (pt >= -2047) & (pt <= 2048) & (nt >= -2047) & (nt <= 2048)
+    if half.all():
+        return ranc.RANC_POTENTIAL_FP16
+    if (hi <= 32767).all() and (lo >= -32768).all():
+        return ranc.RANC_POTENTIAL_INT16
+    return ranc.RANC_POTENTIAL_INT32
+
+
+def per_tick_parity(ranc, oracle_mod, net, x, T, fmt=None):
     B = x.shape[0]
     ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
     sim = ranc.Sim(net, B, ranc.RANC_PATH_BATCHED)
+    if fmt is not None:
+        assert sim.potential_format() == fmt
     sim.load_inputs(x)
     v, s, d = gpu_trace(sim, T)
     for t in range(T):
@@ -44,7 +62,7 @@ def per_tick_parity(ranc, oracle_mod, net, x, T):
 def test_tiny_workload_one_padded_tile(ranc, oracle_mod):
     net = W.tiny_5core()
     x = W.rate_coded_inputs(net.meta["seed"], 64, 8, 784, 0.15)
-    per_tick_parity(ranc, oracle_mod, net, x, 9)
+    per_tick_parity(ranc, oracle_mod, net, x, 9, fmt=ranc.RANC_POTENTIAL_FP16)
 
 
 SHAPES = [
@@ -63,7 +81,7 @@ def test_random_nets_every_tick(ranc, oracle_mod, shape):
                        v0=v0, n_inputs=90, fanout_per_line=4, p_core=0.6, p_out=0.2, w_lim=wl,
                        weight_bits=wb, pthr=(1, 3 * wl), nthr=(-3 * wl, -1), leak=(-2, 2))
     x = W.rate_coded_inputs(9, B, 10, net.n_inputs, 0.3)
-    ref = per_tick_parity(ranc, oracle_mod, net, x, 18)
+    ref = per_tick_parity(ranc, oracle_mod, net, x, 18, fmt=expected_format(ranc, net))
     assert ref["counters"][:, 1].sum() > 0
 
 
@@ -71,7 +89,42 @@ def test_int32_potentials_when_int16_cannot_hold_them(ranc, oracle_mod):
     net = W.random_net(301, 2, 1, axons=64, neurons=128, w_lim=2047, weight_bits=12, pthr=(30000, 60000),
                        nthr=(-60000, -30000), leak=(-5, 5), n_inputs=40, fanout_per_line=6)
     x = W.rate_coded_inputs(10, 150, 8, net.n_inputs, 0.5)
-    per_tick_parity(ranc, oracle_mod, net, x, 12)
+    per_tick_parity(ranc, oracle_mod, net, x, 12, fmt=ranc.RANC_POTENTIAL_INT32)
+
+
+def fp16_edge_net(seed, neg_mode, pthr_hi=2048):
+    """Thresholds and values at the edges of the fp16 format's conditions:
+    theta+ up to 2048, theta- down to -2047, leak in [-1, 1] so that V + leak
+    reaches +-2048, weights of 12 bits so that V + dV overflows fp16 (to
+    +-inf) when many axons are active; a few neurons carry reset / v0 at
+    +-2048 with zero leak."""
+    net = W.random_net(seed, 2, 2, axons=128, neurons=128, n_types=4, density=0.6, w_lim=2047, weight_bits=12,
+                       pthr=(1900, pthr_hi), nthr=(-2047, -1900), leak=(-1, 1), reset=(-2047, 2047),
+                       neg_mode=neg_mode, v0=(-1500, 1500), n_inputs=64, fanout_per_line=16, p_core=0.6,
+                       p_out=0.2, delay_max=3)
+    net.leak[:, :8] = 0
+    net.reset[:, 0], net.reset[:, 1] = 2048, -2048
+    net.v0[:, 2], net.v0[:, 3] = 2048, -2048
+    net.pos_thr[:, 4], net.neg_thr[:, 4] = 2048, -2047
+    net.pos_thr[:, 5], net.neg_thr[:, 5] = -2047, -2047   # theta+ <= theta-: fires at any x >= -2047
+    return net
+
+
+@pytest.mark.parametrize("neg_mode", [0, 1])
+def test_fp16_potentials_at_the_edges_of_their_range(ranc, oracle_mod, neg_mode):
+    net = fp16_edge_net(311 + neg_mode, neg_mode)
+    x = W.rate_coded_inputs(12, 140, 10, net.n_inputs, 0.5)
+    ref = per_tick_parity(ranc, oracle_mod, net, x, 14, fmt=ranc.RANC_POTENTIAL_FP16)
+    v = ref["v_trace"]
+    assert v.max() >= 2000 and v.min() <= -2000          # the extremes are reached
+    assert ref["counters"][:, 0].sum() > 0
+
+
+def test_int16_potentials_one_past_the_fp16_range(ranc, oracle_mod):
+    net = fp16_edge_net(313, 0, pthr_hi=2049)
+    assert net.pos_thr.max() == 2049
+    x = W.rate_coded_inputs(13, 130, 10, net.n_inputs, 0.5)
+    per_tick_parity(ranc, oracle_mod, net, x, 12, fmt=ranc.RANC_POTENTIAL_INT16)
 
 
 SAMPLED = [0, 1, 127, 128, 1000, 2047, 2048, 3001, 4094, 4095]
