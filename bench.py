@@ -296,6 +296,56 @@ def bench_truenorth(ranc, torch, steps, warmup):
                              "cores": 1, "kind": "oracle", "sample": "2 ticks of one sample"}}
 
 
+STREAM_FRAMES, STREAM_TICKS = 10000, 10010
+
+
+def bench_stream(ranc, torch, steps, warmup):
+    """Table I's streamed MNIST-512c run: the 512-core net, one new 28x28
+    frame per tick for 10 000 ticks, 10 010 ticks in all, the output bus
+    logged every tick; plain path, batch 1, one persistent launch.  A step is
+    one whole run (inputs and log in device memory)."""
+    import ranc_workloads as W
+    import oracle
+    net = W.mnist_512core()
+    x = W.rate_coded_inputs(net.meta["seed"] + 7, 1, STREAM_FRAMES, 784, 0.15)
+    dx = torch.from_numpy(x.view(np.int32)).cuda()
+    dlog = torch.zeros((1, STREAM_TICKS, net.n_outputs), dtype=torch.int32, device="cuda")
+    sim = ranc.Sim(net, 1, ranc.RANC_PATH_PLAIN)
+    run = lambda: ranc.ranc_run_stream(sim.h, dx.data_ptr(), STREAM_FRAMES, STREAM_TICKS, dlog.data_ptr(),
+                                       ranc.RANC_MEM_DEVICE)
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    l0 = ranc.ranc_launch_count(sim.h)
+    ms = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    launches = ranc.ranc_launch_count(sim.h) - l0
+    events = int(dlog.sum().item())
+    sim.close()
+    oracle.build()
+    t0 = time.perf_counter()
+    n_cpu = 48
+    oracle.run(net, x[:, :n_cpu], n_cpu, n_threads=1)
+    per_tick_cpu = (time.perf_counter() - t0) / n_cpu
+    sec = ms / steps / 1e3
+    return {"metric": "streamed MNIST-512c-shaped run: seconds per 10 010-tick stream (512 cores 256x256, one new "
+                      "frame per tick, output bus logged every tick)",
+            "value": sec, "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "dtype": "int32", "data": "synthetic (rate-coded 28x28 frames, p=0.15)",
+            "config": {"workload": "mnist-shaped 512-core net, 10 000 frames, 10 010 ticks, batch 1",
+                       "path": "plain, one persistent cooperative launch"},
+            "avg_tick_us": 1e6 * sec / STREAM_TICKS, "output_events": events, "gpu_launches": launches,
+            "paper_context": {"serial_cpu_s": 20344, "gpu_speedup": 780, "hardware": "EPYC 7552 one core vs V100S"},
+            "cpu_baseline": {"value": per_tick_cpu * STREAM_TICKS, "unit": "s (extrapolated from 48 ticks)",
+                             "cores": 1, "kind": "oracle", "sample": "the first 48 ticks of the stream"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,8 +357,9 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse"],
+    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream"],
                     help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1; "
+                         "stream: Table I's streamed 10 010-tick MNIST-512c shape, one frame per tick; "
                          "dse: surrogate-ranked design-space exploration (512 training points, 20000 candidates)")
     args = ap.parse_args()
     rank, ws, local = dist_env()
@@ -352,6 +403,10 @@ def main():
     if args.workload == "truenorth":
         if rank == 0:
             print(json.dumps(bench_truenorth(ranc, torch, args.steps, args.warmup)))
+        return
+    if args.workload == "stream":
+        if rank == 0:
+            print(json.dumps(bench_stream(ranc, torch, args.steps, args.warmup)))
         return
     if args.workload == "dse":
         if rank == 0:

@@ -201,6 +201,22 @@ int ranc_reset(ranc_sim *sim);
 int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in, int32_t window,
                      uint32_t *counts, int32_t mem);
 
+/* Streaming, the shape of the paper's MNIST and CIFAR-10 runs (Table I: 10 010
+ * ticks, one new image presented per tick and carried through the layers
+ * while the next ones enter; the output bus is logged every tick, Sec. IV).
+ * Resets the handle as ranc_reset does except for the counters, which keep
+ * accumulating; inputs[b][k][words] become the input lines of tick k for
+ * k < n_in (no input after); n_ticks ticks are simulated; out_ticks[b][t][id]
+ * receives the number of output-bus events of id during tick t (so a stream
+ * of frames yields, per frame, the events of the ticks it reaches the bus).
+ * ranc_read_outputs afterwards returns the sums over the run.  `mem` says
+ * whether `inputs` and `out_ticks` are host (synchronous) or device
+ * (stream-ordered) memory.  Plain path: one persistent cooperative launch
+ * when the grid fits on the device, per-tick launches otherwise; batched
+ * path: per-tick launches (each of the batch's samples is its own stream). */
+int ranc_run_stream(ranc_sim *sim, const uint32_t *inputs, int32_t n_in, int32_t n_ticks, uint32_t *out_ticks,
+                    int32_t mem);
+
 /* Checkpoint.  ranc_save_state with buf == NULL stores the needed size in *n;
  * otherwise *n must be at least that size and the state after the last
  * completed tick (tick, V, schedulers, outputs, counters, last spikes) is

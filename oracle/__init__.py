@@ -56,7 +56,7 @@ def _load():
         _lib.oracle_run.restype = C.c_int
         _lib.oracle_run.argtypes = [C.POINTER(_Net), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                    C.c_int32, C.c_char_p, C.c_int32]
+                                    C.c_void_p, C.c_int32, C.c_char_p, C.c_int32]
         _lib.oracle_max_threads.restype = C.c_int
     return _lib
 
@@ -69,14 +69,15 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def run(net, inputs, n_ticks, trace=False, n_threads=1):
+def run(net, inputs, n_ticks, trace=False, n_threads=1, out_trace=False):
     """Simulate every sample of ``inputs`` ([S, T_in, words] uint32) for
     ``n_ticks`` ticks from the initial state.
 
     Returns a dict with ``v`` [S, C, N] int32 (after the last tick),
-    ``out`` [S, n_outputs] uint32, ``counters`` [S, 5] uint64 and, when
+    ``out`` [S, n_outputs] uint32, ``counters`` [S, 5] uint64; when
     ``trace``, ``v_trace`` [S, n_ticks, C, N] int32 and ``spike_trace``
-    [S, n_ticks, C, N] uint8.
+    [S, n_ticks, C, N] uint8; when ``out_trace``, ``out_trace``
+    [S, n_ticks, n_outputs] uint32 (output-bus events of every tick).
     """
     lib = _load()
     inputs = np.ascontiguousarray(inputs, dtype=np.uint32)
@@ -102,12 +103,15 @@ def run(net, inputs, n_ticks, trace=False, n_threads=1):
     cnt = np.zeros((S, 5), dtype=np.uint64)
     vt = np.zeros((S, n_ticks, Cn, N), dtype=np.int32) if trace else None
     st = np.zeros((S, n_ticks, Cn, N), dtype=np.uint8) if trace else None
+    ot = np.zeros((S, n_ticks, net.n_outputs), dtype=np.uint32) if out_trace else None
     err = C.create_string_buffer(512)
     rc = lib.oracle_run(C.byref(s), S, _ptr(inputs), t_in, int(n_ticks), _ptr(v), _ptr(out), _ptr(cnt),
-                        _ptr(vt), _ptr(st), int(n_threads), err, 512)
+                        _ptr(vt), _ptr(st), _ptr(ot), int(n_threads), err, 512)
     if rc != 0:
         raise ValueError(f"oracle_run failed ({rc}): {err.value.decode()}")
     res = dict(v=v, out=out, counters=cnt)
     if trace:
         res.update(v_trace=vt, spike_trace=st)
+    if out_trace:
+        res.update(out_trace=ot)
     return res

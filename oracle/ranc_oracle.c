@@ -87,9 +87,10 @@ static uint8_t *row(const oracle_net *net, oracle_state *st, int c, int r)
 }
 
 /* One tick of Alg. 1 for one sample.  in_bits = this tick's input line bits
- * (NULL when the sample has no input at this tick). */
+ * (NULL when the sample has no input at this tick); out_tick, when not NULL,
+ * also receives this tick's output-bus events per id. */
 static int oracle_tick(const oracle_net *net, oracle_state *st, const uint32_t *in_bits,
-                       uint32_t *out_counts, uint64_t *cnt, char *err, int errlen)
+                       uint32_t *out_counts, uint32_t *out_tick, uint64_t *cnt, char *err, int errlen)
 {
     const int C = net->n_cores, A = net->axons, N = net->neurons;
 
@@ -166,6 +167,7 @@ static int oracle_tick(const oracle_net *net, oracle_state *st, const uint32_t *
                     return -1;
                 }
                 out_counts[net->dest_axon[cn]]++;
+                if (out_tick) out_tick[net->dest_axon[cn]]++;
                 cnt[C_OUTPUTS]++;
             }
         }
@@ -182,13 +184,17 @@ static int oracle_tick(const oracle_net *net, oracle_state *st, const uint32_t *
  *   counters    [n_samples][5] (spikes, packets, outputs, synaptic events, ticks)
  *   v_trace     [n_samples][n_ticks][cores][neurons] or NULL
  *   spike_trace [n_samples][n_ticks][cores][neurons] (0/1) or NULL
+ *   out_trace   [n_samples][n_ticks][n_outputs] output-bus events of each
+ *               tick (the output file of a streamed run, Sec. IV), zeroed by
+ *               the caller, or NULL
  *   n_threads   samples are independent; > 1 runs them on OpenMP threads
  * Returns 0, -1 (invalid network) or -2 (potential outside int32); err holds
  * the reason.
  */
 int oracle_run(const oracle_net *net, int32_t n_samples, const uint32_t *inputs, int32_t t_in,
                int32_t n_ticks, int32_t *v_final, uint32_t *out_counts, uint64_t *counters,
-               int32_t *v_trace, uint8_t *spike_trace, int32_t n_threads, char *err, int32_t errlen)
+               int32_t *v_trace, uint8_t *spike_trace, uint32_t *out_trace, int32_t n_threads, char *err,
+               int32_t errlen)
 {
     const int C = net->n_cores, N = net->neurons;
     const int words = (net->n_inputs + 31) / 32;
@@ -230,7 +236,8 @@ int oracle_run(const oracle_net *net, int32_t n_samples, const uint32_t *inputs,
         int rc = 0;
         for (int t = 0; t < n_ticks && rc == 0; t++) {
             const uint32_t *in = (t < t_in) ? inputs + ((size_t)smp * t_in + t) * words : NULL;
-            rc = oracle_tick(net, &st, in, oc, cnt, lerr, sizeof lerr);
+            uint32_t *ot = out_trace ? out_trace + ((size_t)smp * n_ticks + t) * net->n_outputs : NULL;
+            rc = oracle_tick(net, &st, in, oc, ot, cnt, lerr, sizeof lerr);
             if (rc) break;
             size_t base = ((size_t)smp * n_ticks + t) * C * N;
             for (size_t i = 0; i < (size_t)C * N; i++) {

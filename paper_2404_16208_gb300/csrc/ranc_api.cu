@@ -156,7 +156,7 @@ bool validate(const ranc_desc *d, int batch, int path, std::vector<int> &core_at
 void free_all(ranc_sim *s) {
     void *ptrs[] = {s->xbarT, s->tmask, s->wnk, s->prm, s->dst, s->in_ptr, s->in_line, s->in_axon, s->v0,
                     s->V, s->ring, s->spk, s->out, s->cnt, s->inputs, s->err, s->digest, s->stage,
-                    s->gbar, s->counts_dev};
+                    s->gbar, s->counts_dev, s->olog_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     batched_teardown(s);
@@ -238,6 +238,7 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
             a.inputs = sim->in_override ? sim->in_override : sim->inputs;
             a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
             a.stall_test = sim->stall_test;
+            a.olog = sim->olog_t; a.olog_stride = sim->olog_stride;
             e = launch_plain_tick(a, sim->stream);
         } else {
             BatchedArgs a{};
@@ -758,6 +759,114 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
     sim->n_valid = sim->B;
     sim->in_ticks = 0;  // the window inputs are not kept as the handle's schedule
     if (mem == RANC_MEM_HOST) return sync_and_check(sim);
+    return RANC_OK;
+}
+
+// Streaming: one persistent cooperative launch of the plain window kernel
+// over the whole stream (inputs read from global memory every tick).
+static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in, int n_ticks, uint32_t *dev_log) {
+    WindowArgs w{};
+    w.G = std::min(kMaxWindowCores, std::max(1, 1024 / sim->N));
+    w.n_groups = (sim->C + w.G - 1) / w.G;
+    w.n_samples = sim->B;
+    w.t_in = n_in;
+    w.window = n_ticks;
+    w.v0 = sim->v0;
+    w.bar = sim->gbar;
+    w.counts = nullptr;
+    w.stream = 1;
+    w.olog = dev_log;
+    PlainArgs &a = w.p;
+    a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
+    a.B = sim->B; a.n_valid = sim->B; a.in_words = sim->in_words; a.in_ticks = n_in;
+    a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = 0;
+    a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+    a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
+    a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (sim->timing) {
+        if (sim->ev_used + 2 > 4096) {
+            int rc = fold_timing(sim);
+            if (rc) return rc;
+        }
+        e0 = next_event(sim);
+        e1 = next_event(sim);
+        if (!e0 || !e1) return fail(sim, RANC_ECUDA, "cudaEventCreate failed");
+        CUDA_OR_FAIL(sim, cudaEventRecord(e0, sim->stream));
+    }
+    cudaError_t e = launch_plain_windows(w, sim->stream);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        if (sim->timing) sim->ev_used -= 2;
+        return RANC_ENOTSUP;
+    }
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "persistent stream kernel: %s", cudaGetErrorString(e));
+    if (sim->timing) {
+        CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+        sim->ev_ticks.push_back((long long)n_ticks);
+    }
+    sim->launches++;
+    sim->tick = n_ticks;
+    sim->ticks_total += (unsigned long long)n_ticks * sim->B;
+    sim->in_ticks = 0;
+    return RANC_OK;
+}
+
+extern "C" int ranc_run_stream(ranc_sim *sim, const uint32_t *inputs, int32_t n_in, int32_t n_ticks,
+                               uint32_t *out_ticks, int32_t mem) {
+    CHECK_LIVE(sim);
+    if (n_in < 0 || n_ticks < 0 || (n_in > 0 && !inputs) || (n_ticks > 0 && !out_ticks) ||
+        (mem != RANC_MEM_HOST && mem != RANC_MEM_DEVICE))
+        return fail(sim, RANC_EINVAL, "bad run_stream arguments");
+    const size_t lwords = (size_t)sim->B * n_ticks * sim->n_outputs;
+    uint32_t *dev_log = out_ticks;
+    if (mem == RANC_MEM_HOST && lwords > 0) {
+        if (lwords > sim->olog_cap) {
+            CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+            if (sim->olog_dev) cudaFree(sim->olog_dev);
+            sim->olog_dev = nullptr;
+            sim->olog_cap = 0;
+            if (dmalloc(&sim->olog_dev, lwords) != cudaSuccess) return fail(sim, RANC_ENOMEM, "output log buffer");
+            sim->olog_cap = lwords;
+        }
+        dev_log = sim->olog_dev;
+    }
+    if (lwords > 0) CUDA_OR_FAIL(sim, cudaMemsetAsync(dev_log, 0, lwords * 4, sim->stream));
+    int rc = RANC_ENOTSUP;
+    if (sim->path == RANC_PATH_PLAIN) {
+        // Inputs on the device as [B][n_in][words] for the persistent kernel.
+        const size_t in_words = (size_t)sim->B * n_in * sim->in_words;
+        const uint32_t *dev_in = inputs;
+        if (mem == RANC_MEM_HOST && in_words > 0) {
+            rc = ensure_stage(sim, in_words);
+            if (rc) return rc;
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->stage, inputs, in_words * 4, cudaMemcpyHostToDevice, sim->stream));
+            dev_in = sim->stage;
+        }
+        rc = run_stream_persistent(sim, dev_in, n_in, n_ticks, dev_log);
+        if (rc != RANC_OK && rc != RANC_ENOTSUP) return rc;
+    }
+    if (rc == RANC_ENOTSUP) {  // per-tick launches: reset, input schedule, one log slot per tick
+        rc = reset_state(sim, false);
+        if (rc) return rc;
+        rc = mem == RANC_MEM_DEVICE ? load_inputs_dev(sim, n_in > 0 ? inputs : nullptr, sim->B, n_in)
+                                    : load_inputs_host(sim, n_in > 0 ? inputs : nullptr, sim->B, n_in);
+        if (rc) return rc;
+        sim->olog_stride = (long long)n_ticks * sim->n_outputs;
+        for (int t = 0; t < n_ticks && rc == RANC_OK; t++) {
+            sim->olog_t = dev_log + (size_t)t * sim->n_outputs;
+            rc = step_ticks(sim, 1);
+        }
+        sim->olog_t = nullptr;
+        sim->olog_stride = 0;
+        sim->in_ticks = 0;  // the stream's inputs are not kept as the handle's schedule
+        if (rc) return rc;
+    }
+    if (mem == RANC_MEM_HOST) {
+        if (lwords > 0)
+            CUDA_OR_FAIL(sim, cudaMemcpyAsync(out_ticks, dev_log, lwords * 4, cudaMemcpyDeviceToHost, sim->stream));
+        return sync_and_check(sim);
+    }
     return RANC_OK;
 }
 

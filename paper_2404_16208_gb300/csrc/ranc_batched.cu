@@ -73,6 +73,9 @@ struct TickArgs {
     unsigned long long *cnt;
     int *err;
     uint32_t tmem_cols;
+    uint32_t *olog;          // NULL, or this tick's output-bus log: sample b < olog_rows, id -> olog[b * olog_stride + id]
+    long long olog_stride;
+    int olog_rows;
 };
 
 // ---------------------------------------------------------------------------
@@ -324,8 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         const int cc0 = NH == 2 ? (g & 1) * 2 : g;
         const int n = h * 128 + q * 32 + lane;
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
-        constexpr int kPre = sizeof(VT) == 2 ? 2 : 1;      // units whose potentials are loaded early
         constexpr bool kHalf = std::is_same<VT, __half>::value;
+        // Units whose potentials are loaded before the build: both for int16
+        // (registers allow it); one for int32 and fp16 (the fp16 update keeps
+        // more values live, and a second early unit would spill).
+        constexpr int kPre = (sizeof(VT) == 2 && !kHalf) ? 2 : 1;
         VT *Vg = reinterpret_cast<VT *>(a.V);
         // Build task of this lane: axon rax, samples 64*rhf .. 64*rhf+63 (two
         // scheduler words, read as one 8-byte vector: a warp reads 256
@@ -513,8 +519,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                         olanes &= olanes - 1u;
                         const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
                         const uint32_t idL = __shfl_sync(0xffffffffu, dd.x, L);
-                        if ((mL >> lane) & 1u)
-                            atomicAdd(a.out + (size_t)(je * 128 + cc * 32 + lane) * a.n_out + idL, 1u);
+                        const int bs = je * 128 + cc * 32 + lane;
+                        if ((mL >> lane) & 1u) {
+                            atomicAdd(a.out + (size_t)bs * a.n_out + idL, 1u);
+                            if (a.olog && bs < a.olog_rows) atomicAdd(a.olog + (size_t)bs * a.olog_stride + idL, 1u);
+                        }
                     }
                 }
                 tc_fence_before();
@@ -923,6 +932,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.prm = sim->prm; a.dst = sim->dst; a.fin_ptr = bs->fin_ptr; a.fin_line = bs->fin_line; a.outdeg = bs->outdeg;
     a.inT = bs->inT; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
     a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
+    a.olog = sim->olog_t; a.olog_stride = sim->olog_stride; a.olog_rows = sim->B;
     const int grid = std::min(bs->n_sm, a.items);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)

@@ -49,6 +49,8 @@ struct PlainArgs {
     unsigned long long *cnt;     // [B][C][4]    spikes, packets, outputs, synaptic events
     int *err;
     int stall_test;              // test only: CTA (0, 0) waits on an mbarrier nothing arrives on
+    uint32_t *olog;              // NULL, or this tick's output-bus log: event (b, id) also adds 1 at
+    long long olog_stride;       //   olog[b * olog_stride + id]
 };
 
 // Persistent plain path (ranc_run_samples): G cores per CTA, all windows in one launch.
@@ -58,8 +60,10 @@ struct WindowArgs {
     int G, n_groups;             // cores per CTA, CTAs per batch slot
     int n_samples, t_in, window;
     const int *v0;               // [C][N]
-    uint32_t *counts;            // [n_samples][n_out] (device)
+    uint32_t *counts;            // [n_samples][n_out] (device) or NULL
     unsigned *bar;               // [2] grid barrier: arrivals, generation
+    int stream;                  // inputs read from p.inputs every tick instead of staged in shared memory
+    uint32_t *olog;              // NULL, or per-tick output-bus log [n_samples][window][n_out]
 };
 
 // Batched-path device layout (one tile = kTileS samples, sample-minor bits).
@@ -118,6 +122,10 @@ struct ranc_sim {
     unsigned *gbar = nullptr;            // plain: grid barrier of the persistent window kernel
     uint32_t *counts_dev = nullptr;      // plain: device copy of run_samples counts (host mode)
     size_t counts_cap = 0;
+    uint32_t *olog_dev = nullptr;        // run_stream: device copy of the per-tick output log (host mode)
+    size_t olog_cap = 0;
+    uint32_t *olog_t = nullptr;          // run_stream: log slot of the tick being stepped, or NULL
+    long long olog_stride = 0;
     int n_valid = 0;
 
     long long tick = 0;

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
             atomicOr(a.ring + (((size_t)b * a.C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
         } else if (kind == RANC_DEST_OUTPUT) {
             atomicAdd(a.out + (size_t)b * a.n_out + d.x, 1u);
+            if (a.olog) atomicAdd(a.olog + (size_t)b * a.olog_stride + d.x, 1u);
         }
     }
     const unsigned pm = __ballot_sync(0xffffffffu, kind == RANC_DEST_CORE);
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
         for (int i = tid; i < ncores * kRows * AW; i += blockDim.x) __stcg(rows + i, 0u);
         if (grp == 0)
             for (int i = tid; i < a.n_out; i += blockDim.x) __stcg(a.out + (size_t)b * a.n_out + i, 0u);
-        for (int i = tid; i < ipw; i += blockDim.x) inb[i] = valid ? __ldg(a.inputs + (size_t)smp * ipw + i) : 0u;
+        if (!w.stream)
+            for (int i = tid; i < ipw; i += blockDim.x) inb[i] = valid ? __ldg(a.inputs + (size_t)smp * ipw + i) : 0u;
         if (!grid_sync(w.bar, nblocks, gen, &s_ok)) break;
         bool stop = false;
         for (int t = 0; t < w.window; ++t) {
@@ -271,7 +273,10 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
             }
             __syncthreads();
             if (valid && t < w.t_in) {
-                const uint32_t *in = inb + (size_t)t * a.in_words;
+                // Inputs of tick t: staged in shared memory, or (streaming) read
+                // from the caller's array, one frame per tick.
+                const uint32_t *in = w.stream ? a.inputs + ((size_t)smp * w.t_in + t) * a.in_words
+                                              : inb + (size_t)t * a.in_words;
                 for (int k = ip0 + tid; k < ip1; k += blockDim.x) {
                     const int L = a.in_line[k];
                     if ((in[L >> 5] >> (L & 31)) & 1u) {
@@ -324,7 +329,11 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                         if (valid) ++n_pk;
                     } else if (kind == RANC_DEST_OUTPUT) {
                         atomicAdd(a.out + (size_t)b * a.n_out + dd.x, 1u);
-                        if (valid) ++n_ou;
+                        if (valid) {
+                            ++n_ou;
+                            if (w.olog)
+                                atomicAdd(w.olog + ((size_t)smp * w.window + t) * a.n_out + dd.x, 1u);
+                        }
                     }
                 }
             }
@@ -336,7 +345,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
             }
         }
         if (stop) break;
-        if (grp == 0 && valid)
+        if (grp == 0 && valid && w.counts)
             for (int i = tid; i < a.n_out; i += blockDim.x)
                 w.counts[(size_t)smp * a.n_out + i] = __ldcg(a.out + (size_t)b * a.n_out + i);
         if (!grid_sync(w.bar, nblocks, gen, &s_ok)) break;
@@ -367,7 +376,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     const int threads = w.G * w.p.N;
     const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + (size_t)w.G * w.p.AW +
-                         (size_t)w.t_in * w.p.in_words) * 4;
+                         (w.stream ? 0 : (size_t)w.t_in * w.p.in_words)) * 4;
     cudaError_t e = cudaFuncSetAttribute(plain_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 0, per_sm = 0;

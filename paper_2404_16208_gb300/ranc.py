@@ -22,7 +22,7 @@ COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
 EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_get_tick", "ranc_reset",
-            "ranc_run_samples", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
+            "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
             "ranc_read_kernel_timing", "ranc_launch_count", "ranc_potential_format", "ranc_destroy",
             "ranc_last_error")
 RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
@@ -67,6 +67,7 @@ def load_library(path=LIB_PATH):
         "ranc_get_tick": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_reset": ([vp], C.c_int),
         "ranc_run_samples": ([vp, vp, i32, i32, i32, vp, i32], C.c_int),
+        "ranc_run_stream": ([vp, vp, i32, i32, vp, i32], C.c_int),
         "ranc_save_state": ([vp, vp, C.POINTER(C.c_size_t)], C.c_int),
         "ranc_load_state": ([vp, vp, C.c_size_t], C.c_int),
         "ranc_set_kernel_timing": ([vp, i32], C.c_int),
@@ -192,6 +193,18 @@ def ranc_run_samples(h, inputs, n_samples, t_in, window, counts, mem=RANC_MEM_HO
     _check(_lib.ranc_run_samples(h, ip, int(n_samples), int(t_in), int(window), cp, int(mem)), h)
 
 
+def ranc_run_stream(h, inputs, n_in, n_ticks, out_ticks, mem=RANC_MEM_HOST):
+    """Host mode: ``inputs`` uint32 [B, n_in, words] and ``out_ticks`` uint32
+    [B, n_ticks, n_outputs] numpy arrays.  Device mode: both are device pointers."""
+    if mem == RANC_MEM_HOST:
+        inputs = _c(inputs, np.uint32) if inputs is not None else None
+        assert out_ticks.dtype == np.uint32 and out_ticks.flags.c_contiguous
+        ip, op = (_p(inputs) if inputs is not None else None), _p(out_ticks)
+    else:
+        ip, op = C.c_void_p(int(inputs)), C.c_void_p(int(out_ticks))
+    _check(_lib.ranc_run_stream(h, ip, int(n_in), int(n_ticks), op, int(mem)), h)
+
+
 def ranc_save_state(h):
     n = C.c_size_t(0)
     _check(_lib.ranc_save_state(h, None, C.byref(n)), h)
@@ -271,6 +284,13 @@ class Sim:
         counts = np.zeros((inputs.shape[0], self.net.n_outputs), np.uint32)
         ranc_run_samples(self.h, inputs, inputs.shape[0], inputs.shape[1], window, counts)
         return counts
+
+    def run_stream(self, inputs, n_ticks):
+        """inputs [B, n_in, words] -> per-tick output-bus counts [B, n_ticks, n_outputs]."""
+        inputs = _c(inputs, np.uint32)
+        out = np.zeros((self.batch, n_ticks, self.net.n_outputs), np.uint32)
+        ranc_run_stream(self.h, inputs, inputs.shape[1], n_ticks, out)
+        return out
 
     def potential_format(self):
         """RANC_POTENTIAL_INT32, _INT16 or _FP16: how the potentials are stored."""

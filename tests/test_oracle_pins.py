@@ -294,6 +294,48 @@ def test_tiny_workload_matrix_identity_and_conservation(oracle_mod):
     check_conservation(net, r)
 
 
+def stream_chain_net(delay):
+    """chain_net with core 1 neuron 0 on the output bus (id 0) instead of
+    sending back to core 0."""
+    net = chain_net(delay)
+    net.dest[1, 0] = (0, 0, 0, 1, W.KIND_OUTPUT)
+    return net
+
+
+@pytest.mark.parametrize("d", [1, 3, 15])
+def test_stream_output_log_timing(oracle_mod, d):
+    """One frame per tick (the streamed runs of Table I): a frame with line 0
+    on at tick t drives core 0 at t (input delay 0), core 1 at t + d, and the
+    bus logs one event of id 0 at tick t + d; frames at neighbouring ticks
+    stay separate in the log.  Derived by hand from the tick rules."""
+    frames = [2, 5, 6, 11]
+    T = 11 + d + 3
+    r = oracle_mod.run(stream_chain_net(d), bits_inputs([1 if t in frames else 0 for t in range(12)]), T,
+                       out_trace=True)
+    log = r["out_trace"][0, :, 0]
+    assert np.flatnonzero(log).tolist() == [t + d for t in frames]
+    assert log.sum() == len(frames) == r["out"][0, 0]
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_output_log_equals_output_spikes_of_each_tick(oracle_mod, seed):
+    """The per-tick log sums to the window counts and, tick by tick, equals
+    the number of spiking output-kind neurons of each id."""
+    net = W.random_net(seed, 3, 2, axons=32, neurons=64, n_types=3, n_inputs=40, fanout_per_line=3,
+                       delay_max=4, p_out=0.4, n_outputs=6)
+    x = W.rate_coded_inputs(seed, 3, 12, net.n_inputs, 0.3)
+    T = 16
+    r = oracle_mod.run(net, x, T, trace=True, out_trace=True)
+    log = r["out_trace"].astype(np.int64)
+    assert log.sum() > 0
+    assert (log.sum(axis=1) == r["out"]).all()
+    st = r["spike_trace"].astype(np.int64)
+    kind = net.dest["kind"]
+    for o in range(net.n_outputs):
+        m = (kind == W.KIND_OUTPUT) & (net.dest["axon"] == o)
+        assert (log[:, :, o] == (st * m).sum(axis=(2, 3))).all(), o
+
+
 def test_zero_spike_special_case(oracle_mod):
     """No input, leak <= 0, positive thresholds, v0 = 0: nothing ever fires
     and V_t = max(neg_thr, t * leak) (the shape of a grid with no mapped
