@@ -346,6 +346,63 @@ def bench_stream(ranc, torch, steps, warmup):
                              "cores": 1, "kind": "oracle", "sample": "the first 48 ticks of the stream"}}
 
 
+def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(16, 128), batch=256, t_in=16, window=32):
+    """A design sweep: n_cfg ragged random networks (core sizes {128, 256,
+    512}^2, weight bits {4, 6, 9}, 2 or 4 axon types, density U[0.1, 0.5],
+    delays U{1..15}, cores U{core_range}, 1024 shared input lines), each run
+    on the same `batch` samples for `window` ticks.  A step simulates every
+    network once.  The autotuned plan (one combined launch per shape class
+    where that is faster) is timed against one handle per network."""
+    import oracle
+    from ranc_workloads import sweep as SW
+    from paper_2404_16208_gb300 import sweep as S
+    t0 = time.perf_counter()
+    nets = SW.sweep(0x5EEDF1, n_cfg, core_range=core_range)
+    gen_s = time.perf_counter() - t0
+    import ranc_workloads as W
+    x = W.rate_coded_inputs(0x5EEDF1, batch, t_in, 1024, 0.15)
+    res = {}
+    for plan in ("auto", "separate"):
+        sw = S.Sweep(nets, batch, plan=plan, probe=64)
+        for _ in range(warmup):
+            outs = sw.run_samples(x, window)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            outs = sw.run_samples(x, window)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / steps
+        res[plan] = dict(seconds=sec, plans=[[list(k), p, len(m)] for k, p, m in sw.plans()], tuning=sw.tuning,
+                         counts=[o.copy() for o in outs], counters=sw.counters().tolist())
+        sw.close()
+    same = all((a == b).all() for a, b in zip(res["auto"]["counts"], res["separate"]["counts"]))
+    events = sum(c[3] for c in res["separate"]["counters"]) / (warmup + steps)
+    # CPU oracle: one sample of the first 4 networks, extrapolated by A*N*cores*samples
+    oracle.build()
+    t0 = time.perf_counter()
+    work_done = 0
+    for n in nets[:4]:
+        oracle.run(n, x[:1, :, :(n.n_inputs + 31) // 32], window, n_threads=1)
+        work_done += n.n_cores * n.axons * n.neurons
+    cpu_s = time.perf_counter() - t0
+    work_all = sum(n.n_cores * n.axons * n.neurons for n in nets) * batch
+    cores = sum(n.n_cores for n in nets)
+    return {"metric": f"design sweep: seconds to simulate {n_cfg} ragged networks x {batch} samples x {window} ticks",
+            "value": res["auto"]["seconds"], "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * res["auto"]["seconds"], "dtype": "per shape class (fp16/int32)",
+            "data": "synthetic", "config": {"workload": f"{n_cfg} networks, {cores} cores in all, sizes "
+                                                        "{128,256,512}^2, 1024 input lines",
+                                            "batch": batch, "window": window, "core_range": list(core_range)},
+            "config_samples_per_s": n_cfg * batch / res["auto"]["seconds"],
+            "synaptic_events_per_s": events / res["auto"]["seconds"],
+            "separate_handles_seconds": res["separate"]["seconds"],
+            "speedup_over_separate": res["separate"]["seconds"] / res["auto"]["seconds"],
+            "identical_results": bool(same), "plans": res["auto"]["plans"], "tuning": res["auto"]["tuning"],
+            "generation_seconds": gen_s,
+            "cpu_baseline": {"value": cpu_s * work_all / work_done, "unit": "s (extrapolated by A*N*cores*samples)",
+                             "cores": 1, "kind": "oracle", "sample": "one sample of the first 4 networks"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +414,7 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream"],
+    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream", "sweep"],
                     help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1; "
                          "stream: Table I's streamed 10 010-tick MNIST-512c shape, one frame per tick; "
                          "dse: surrogate-ranked design-space exploration (512 training points, 20000 candidates)")
@@ -407,6 +464,10 @@ def main():
     if args.workload == "stream":
         if rank == 0:
             print(json.dumps(bench_stream(ranc, torch, args.steps, args.warmup)))
+        return
+    if args.workload == "sweep":
+        if rank == 0:
+            print(json.dumps(bench_sweep(ranc, torch, args.steps, args.warmup)))
         return
     if args.workload == "dse":
         if rank == 0:

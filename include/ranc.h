@@ -182,6 +182,14 @@ int ranc_read_sample_state_noalloc(ranc_sim *sim, int32_t b0, int32_t nb, int32_
  * (ranc_run_samples keeps accumulating across its windows).  Synchronous. */
 int ranc_read_counters(ranc_sim *sim, uint64_t *counters);
 
+/* counters[0..3] (spikes, packets, outputs, synaptic events, as in
+ * ranc_read_counters) of the cores core_begin <= c < core_end only, summed
+ * over the batch since the last ranc_reset.  A description that combines
+ * several independent networks in one grid (a design sweep simulated in one
+ * launch per tick) reads each network's activity this way.  RANC_EINVAL for
+ * a range outside [0, n_cores].  Synchronous. */
+int ranc_read_core_counters(ranc_sim *sim, int32_t core_begin, int32_t core_end, uint64_t *counters);
+
 /* Current tick (counted from the last reset) of every sample. */
 int ranc_get_tick(const ranc_sim *sim, int64_t *tick);
 

@@ -361,10 +361,16 @@ size_t save_size(const ranc_sim *s) {
            (size_t)s->B * s->C * (s->N / 32) * 4 + 4 * 8;
 }
 
-__global__ void reduce_counters_kernel(const unsigned long long *cnt, long long rows, unsigned long long *out) {
+// Sums the per-(sample or tile, core) counters rows [..][C][4] over the rows
+// whose core lies in [c0, c1).
+__global__ void reduce_counters_kernel(const unsigned long long *cnt, long long rows, int C, int c0, int c1,
+                                       unsigned long long *out) {
     unsigned long long acc[4] = {0, 0, 0, 0};
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(r % C);
+        if (c < c0 || c >= c1) continue;
         for (int j = 0; j < 4; j++) acc[j] += cnt[r * 4 + j];
+    }
     for (int j = 0; j < 4; j++) {
         unsigned long long v = acc[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -372,12 +378,13 @@ __global__ void reduce_counters_kernel(const unsigned long long *cnt, long long 
     }
 }
 
-int read_counters4(ranc_sim *sim, unsigned long long *h4) {
+int read_counters4(ranc_sim *sim, unsigned long long *h4, int c0 = 0, int c1 = -1) {
     CUDA_OR_FAIL(sim, cudaMemsetAsync(sim->digest, 0, 5 * 8, sim->stream));
     const long long rows = (long long)(sim->cnt_len / 4);
     long long blocks = std::min<long long>((rows + 255) / 256, 1024);
     if (blocks < 1) blocks = 1;
-    reduce_counters_kernel<<<(unsigned)blocks, 256, 0, sim->stream>>>(sim->cnt, rows, sim->digest + 1);
+    reduce_counters_kernel<<<(unsigned)blocks, 256, 0, sim->stream>>>(sim->cnt, rows, sim->C, c0, c1 < 0 ? sim->C : c1,
+                                                                     sim->digest + 1);
     sim->launches++;
     CUDA_OR_FAIL(sim, cudaGetLastError());
     CUDA_OR_FAIL(sim, cudaMemcpyAsync(h4, sim->digest + 1, 4 * 8, cudaMemcpyDeviceToHost, sim->stream));
@@ -620,6 +627,17 @@ extern "C" int ranc_read_counters(ranc_sim *sim, uint64_t *counters) {
     if (rc) return rc;
     for (int j = 0; j < 4; j++) counters[j] = h4[j];
     counters[RANC_CNT_TICKS] = sim->ticks_total;
+    return RANC_OK;
+}
+
+extern "C" int ranc_read_core_counters(ranc_sim *sim, int32_t core_begin, int32_t core_end, uint64_t *counters) {
+    CHECK_LIVE(sim);
+    if (!counters || core_begin < 0 || core_end < core_begin || core_end > sim->C)
+        return fail(sim, RANC_EINVAL, "bad core range [%d, %d) for %d cores", core_begin, core_end, sim->C);
+    unsigned long long h4[4];
+    int rc = read_counters4(sim, h4, core_begin, core_end);
+    if (rc) return rc;
+    for (int j = 0; j < 4; j++) counters[j] = h4[j];
     return RANC_OK;
 }
 

@@ -911,14 +911,15 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         why = "cuTensorMapEncodeTiled failed";
         return cudaErrorInvalidValue;
     }
+    // The attribute belongs to the kernel, not to this handle: it is only ever
+    // raised, so handles of different shapes can coexist in one process.
     const int sm = (int)bs->smem;
-    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(batched_tick_kernel<__half, 0>, at, sm)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(batched_tick_kernel<__half, 1>, at, sm)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 0>, at, sm)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(batched_tick_kernel<int16_t, 1>, at, sm)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(batched_tick_kernel<int, 0>, at, sm)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(batched_tick_kernel<int, 1>, at, sm)) != cudaSuccess)
+    if ((e = raise_smem_limit((const void *)batched_tick_kernel<__half, 0>, sm)) != cudaSuccess ||
+        (e = raise_smem_limit((const void *)batched_tick_kernel<__half, 1>, sm)) != cudaSuccess ||
+        (e = raise_smem_limit((const void *)batched_tick_kernel<int16_t, 0>, sm)) != cudaSuccess ||
+        (e = raise_smem_limit((const void *)batched_tick_kernel<int16_t, 1>, sm)) != cudaSuccess ||
+        (e = raise_smem_limit((const void *)batched_tick_kernel<int, 0>, sm)) != cudaSuccess ||
+        (e = raise_smem_limit((const void *)batched_tick_kernel<int, 1>, sm)) != cudaSuccess)
         why = "kernel shared-memory attribute";
     return e;
 }

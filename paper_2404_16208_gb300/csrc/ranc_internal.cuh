@@ -156,6 +156,7 @@ void fault_alloc_arm_from_env();
 namespace ranc {
 // Implemented in ranc_plain.cu
 cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s);
+cudaError_t raise_smem_limit(const void *kernel, int bytes);
 cudaError_t plain_setup_kernel_attrs(int N, int AW);
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s);
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);

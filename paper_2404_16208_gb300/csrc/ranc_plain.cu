@@ -377,7 +377,7 @@ cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     const int threads = w.G * w.p.N;
     const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + (size_t)w.G * w.p.AW +
                          (w.stream ? 0 : (size_t)w.t_in * w.p.in_words)) * 4;
-    cudaError_t e = cudaFuncSetAttribute(plain_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit((const void *)plain_window_kernel, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -401,7 +401,17 @@ __global__ void plain_reset_v_kernel(int *V, const int *v0, long long per_sample
 cudaError_t plain_setup_kernel_attrs(int N, int AW) {
     const int smem = N * AW * 4;
     if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(plain_tick_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return raise_smem_limit((const void *)plain_tick_kernel, smem);
+}
+
+// Raises (never lowers) a kernel's dynamic shared-memory limit: the attribute
+// is shared by every handle of the process.
+cudaError_t raise_smem_limit(const void *kernel, int bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters) {

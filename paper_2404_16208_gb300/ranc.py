@@ -21,7 +21,7 @@ RANC_MEM_HOST, RANC_MEM_DEVICE = 0, 1
 COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
 EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
-            "ranc_read_counters", "ranc_get_tick", "ranc_reset",
+            "ranc_read_counters", "ranc_read_core_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
             "ranc_read_kernel_timing", "ranc_launch_count", "ranc_potential_format", "ranc_destroy",
             "ranc_last_error")
@@ -64,6 +64,7 @@ def load_library(path=LIB_PATH):
         "ranc_read_sample_state": ([vp, i32, i32, vp, vp], C.c_int),
         "ranc_read_sample_state_noalloc": ([vp, i32, i32, vp, vp], C.c_int),
         "ranc_read_counters": ([vp, u64p], C.c_int),
+        "ranc_read_core_counters": ([vp, i32, i32, u64p], C.c_int),
         "ranc_get_tick": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_reset": ([vp], C.c_int),
         "ranc_run_samples": ([vp, vp, i32, i32, i32, vp, i32], C.c_int),
@@ -171,6 +172,12 @@ def ranc_read_counters(h):
     return c
 
 
+def ranc_read_core_counters(h, c0, c1):
+    c = np.zeros(4, np.uint64)
+    _check(_lib.ranc_read_core_counters(h, int(c0), int(c1), _p(c)), h)
+    return c
+
+
 def ranc_get_tick(h):
     t = C.c_int64()
     _check(_lib.ranc_get_tick(h, C.byref(t)), h)
@@ -272,6 +279,10 @@ class Sim:
 
     def counters(self):
         return ranc_read_counters(self.h)
+
+    def core_counters(self, c0, c1):
+        """Spikes, packets, outputs, synaptic events of cores [c0, c1)."""
+        return ranc_read_core_counters(self.h, c0, c1)
 
     def tick(self):
         return ranc_get_tick(self.h)
