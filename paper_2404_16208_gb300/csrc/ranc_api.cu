@@ -212,10 +212,6 @@ int fold_timing(ranc_sim *sim) {
 
 int step_ticks(ranc_sim *sim, int n_ticks) {
     for (int t = 0; t < n_ticks; t++) {
-        if (sim->path == RANC_PATH_BATCHED) {
-            cudaError_t ei = batched_inject(sim);
-            if (ei != cudaSuccess) return fail(sim, RANC_ECUDA, "input injection: %s", cudaGetErrorString(ei));
-        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (sim->timing) {
             if (sim->ev_used + 2 > 4096) {
@@ -655,6 +651,7 @@ extern "C" int ranc_reset(ranc_sim *sim) {
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "device unusable: %s", cudaGetErrorString(e));
         cudaMemsetAsync(sim->err, 0, sizeof(int), sim->stream);
         sim->sticky = 0;
+        sim->ring_all_dirty = 1;  // a failed tick may have left any row written
     }
     sim->ev_used = 0;
     sim->in_override = nullptr;

@@ -67,6 +67,7 @@ struct TickArgs {
     const int *fin_ptr, *fin_line;
     const uint16_t *outdeg;
     const uint4 *inT;
+    const int *v0;           // non-NULL: the potentials are still the reset values v0 [C][N] (V is not read)
     void *V;
     uint4 *ring;
     uint32_t *spk, *out;
@@ -244,6 +245,19 @@ __device__ __forceinline__ int v_to_int(VT x) {
     else return (int)x;
 }
 
+// One 16-byte vector of potentials all equal to x (the reset value v0).
+template <typename VT>
+__device__ __forceinline__ uint4 v_splat(int x) {
+    uint32_t w;
+    if constexpr (sizeof(VT) == 2) {
+        const VT e = v_from_int<VT>(x);
+        w = (uint32_t)(*reinterpret_cast<const uint16_t *>(&e)) * 0x10001u;
+    } else {
+        w = (uint32_t)x;
+    }
+    return make_uint4(w, w, w, w);
+}
+
 // Element offset of potential (tile j, core c, neuron n, sample 32*cc + i) in
 // the interleaved layout described at the top of this file.
 template <typename VT>
@@ -345,10 +359,37 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         uint32_t odr = 0u;
         __half2 lam2 = __float2half2_rn(0.f), pth2 = lam2, nth2 = lam2;  // fp16 potentials only
         uint32_t rst2 = 0u;
+        // Input lines of tick t that drive this lane's axon (Alg. 1: the
+        // packets of the current tick are written into the scheduler before
+        // the neuron block): ORed into the row words as they are read.  The
+        // fan-in list [f0, f1) of the axon is kept for the current core.
+        const bool has_in = a.tick < (long long)a.in_ticks;
+        int fc = -1, f0 = 0, f1 = 0, ln0 = 0;
         auto load_words = [&](int it) -> uint2 {
             const int c = it / T, j = it % T;
+            if (!has_task) return make_uint2(0u, 0u);
             const uint2 *row = reinterpret_cast<const uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
-            return has_task ? row[rax * 2 + rhf] : make_uint2(0u, 0u);
+            uint2 w = row[rax * 2 + rhf];
+            if (has_in) {
+                if (c != fc) {
+                    fc = c;
+                    f0 = a.fin_ptr[(size_t)c * (A + 1) + rax];
+                    f1 = a.fin_ptr[(size_t)c * (A + 1) + rax + 1];
+                    ln0 = f1 > f0 ? a.fin_line[f0] : 0;
+                }
+                if (f1 > f0) {
+                    const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
+                    uint2 x = in[(size_t)ln0 * 2];
+                    for (int e = f0 + 1; e < f1; ++e) {
+                        const uint2 y = in[(size_t)a.fin_line[e] * 2];
+                        x.x |= y.x;
+                        x.y |= y.y;
+                    }
+                    w.x |= x.x;
+                    w.y |= x.y;
+                }
+            }
+            return w;
         };
         uint2 wnext = n_items > 0 ? load_words(i0) : make_uint2(0u, 0u);
         for (int li = 0; li <= n_items; ++li) {
@@ -360,13 +401,21 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 return reinterpret_cast<uint4 *>(Vg + v_index<VT>(je, ce, cc0 + k, n & ~31, 0, C, N)) + lane;
             };
             if (le >= 0) {
+                if (a.v0) {  // first tick after a reset: V = v0, nothing to read
+                    const uint4 vz = v_splat<VT>(a.v0[(size_t)ce * N + n]);
 #pragma unroll
-                for (int k = 0; k < kPre; ++k)
-                    if (k < nu) {
-                        const uint4 *vp = vaddr(k);
+                    for (int k = 0; k < kPre; ++k)
 #pragma unroll
-                        for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e * 32];
-                    }
+                        for (int e = 0; e < kVecs; ++e) vb[k][e] = vz;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kPre; ++k)
+                        if (k < nu) {
+                            const uint4 *vp = vaddr(k);
+#pragma unroll
+                            for (int e = 0; e < kVecs; ++e) vb[k][e] = vp[e * 32];
+                        }
+                }
             }
             // ---- (1) build S of item li
             if (li < n_items) {
@@ -435,9 +484,15 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     if (k >= nu) break;
                     const int cc = cc0 + k;
                     if (k >= kPre) {
-                        const uint4 *vp = vaddr(k);
+                        if (a.v0) {
+                            const uint4 vz = v_splat<VT>(a.v0[(size_t)ce * N + n]);
 #pragma unroll
-                        for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e * 32];
+                            for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vz;
+                        } else {
+                            const uint4 *vp = vaddr(k);
+#pragma unroll
+                            for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e * 32];
+                        }
                     }
                     uint4 *vout = vaddr(k);
                     uint32_t mask = 0u;
@@ -641,36 +696,6 @@ __global__ void transpose_inputs(const uint32_t *x, int n_samples, int ticks, in
 
 // Canonical copies of samples [b0, b0 + nb): v [nb][C][N], spk [nb][C][N/32],
 // ring [nb][C][16][A/32] (ring may be NULL).
-// ORs the input lines of ticks [tau0, tau1) into scheduler rows tau mod 16
-// for every tile: ring[j][c][tau&15][a] |= OR of inT[j][tau][line] over the
-// lines that drive (c, a) (Alg. 1: the packets of the current tick are
-// written into the scheduler before the neuron block).
-__global__ void inject_inputs(const uint4 *inT, int in_ticks, int Lpad, int tau0, int tau1, int T, int C, int A,
-                              const int *inj_ca, const int *inj_ptr, const int *fin_line, int n_pairs, uint4 *ring) {
-    const long long total = (long long)(tau1 - tau0) * T * n_pairs;
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total; f += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(f % n_pairs);
-        const int j = (int)((f / n_pairs) % T);
-        const int tau = tau0 + (int)(f / n_pairs / T);
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        for (int e = inj_ptr[k]; e < inj_ptr[k + 1]; ++e) {
-            const uint4 I = inT[((size_t)j * in_ticks + tau) * Lpad + fin_line[e]];
-            w.x |= I.x;
-            w.y |= I.y;
-            w.z |= I.z;
-            w.w |= I.w;
-        }
-        const int c = inj_ca[k] / A, ax = inj_ca[k] % A;
-        uint4 *r = ring + (((size_t)j * C + c) * kRows + (tau & (kRows - 1))) * A + ax;
-        uint4 o = *r;
-        o.x |= w.x;
-        o.y |= w.y;
-        o.z |= w.z;
-        o.w |= w.w;
-        *r = o;
-    }
-}
-
 template <typename VT>
 __global__ void export_state(const VT *Vb, const uint32_t *spkb, const uint32_t *ringb, int b0, int nb, int C, int N,
                              int A, int *v, uint32_t *spk, uint32_t *ring) {
@@ -748,8 +773,6 @@ struct Batched {
     size_t smem = 0;
     __half *wfold = nullptr;
     int *fin_ptr = nullptr, *fin_line = nullptr;
-    int *inj_ca = nullptr, *inj_ptr = nullptr;  // (core, axon) pairs fed by input lines, CSR into fin_line
-    int n_pairs = 0;
     uint16_t *outdeg = nullptr;
     uint4 *inT = nullptr;
     size_t inT_cap = 0;
@@ -815,6 +838,11 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
             fitsh = false;
     }
     sim->vmode = fitsh ? kVHalf : fits16 ? kVInt16 : kVInt32;
+    // Largest delay of a core-to-core packet: bounds the scheduler rows that
+    // can still hold deliveries when the handle is reset.
+    sim->max_delay = 0;
+    for (size_t i = 0; i < (size_t)C * N; i++)
+        if (d->dest[i].kind == RANC_DEST_CORE) sim->max_delay = std::max<int>(sim->max_delay, d->dest[i].delay);
 
     // Folded weights W[c][n][a] = connected(a, n) ? w[type(a)][n] : 0 (fp16, exact).
     std::vector<__half> wf((size_t)C * N * A);
@@ -848,24 +876,6 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         }
         if (fline.empty()) fline.push_back(0);
     }
-    std::vector<int> inj_ca, inj_ptr(1, 0);
-    for (int c = 0; c < C; c++)
-        for (int ax = 0; ax < A; ax++) {
-            const int f0 = fptr[(size_t)c * (A + 1) + ax], f1 = fptr[(size_t)c * (A + 1) + ax + 1];
-            if (f1 > f0) {
-                inj_ca.push_back(c * A + ax);
-                inj_ptr.push_back(f1);
-            }
-        }
-    // inj_ptr holds end offsets; make it a CSR with the start of the first pair
-    std::vector<int> inj_csr(inj_ca.size() + 1, 0);
-    for (size_t k = 0; k < inj_ca.size(); k++) {
-        const int c = inj_ca[k] / A, ax = inj_ca[k] % A;
-        inj_csr[k] = fptr[(size_t)c * (A + 1) + ax];
-        inj_csr[k + 1] = fptr[(size_t)c * (A + 1) + ax + 1];
-    }
-    bs->n_pairs = (int)inj_ca.size();
-    if (inj_ca.empty()) inj_ca.push_back(0);
     const size_t vsz = sim->vmode == kVInt32 ? 4 : 2;
     if (dev_alloc((void **)&bs->wfold, wf.size() * 2) != cudaSuccess || dev_alloc((void **)&bs->outdeg, od.size() * 2) != cudaSuccess ||
         dev_alloc((void **)&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
@@ -882,11 +892,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     if ((e = cudaMemcpy(bs->wfold, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->fin_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = dev_alloc((void **)&bs->inj_ca, inj_ca.size() * 4)) != cudaSuccess ||
-        (e = dev_alloc((void **)&bs->inj_ptr, inj_csr.size() * 4)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->inj_ca, inj_ca.data(), inj_ca.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->inj_ptr, inj_csr.data(), inj_csr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
         why = "copy of the batched network arrays";
         return e;
     }
@@ -931,7 +937,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.n_valid = sim->n_valid; a.Lpad = bs->Lpad; a.in_ticks = bs->inT ? sim->in_ticks : 0; a.n_out = sim->n_outputs;
     a.neg_mode = sim->neg_mode; a.items = sim->T * sim->C; a.tick = sim->tick;
     a.prm = sim->prm; a.dst = sim->dst; a.fin_ptr = bs->fin_ptr; a.fin_line = bs->fin_line; a.outdeg = bs->outdeg;
-    a.inT = bs->inT; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
+    a.inT = bs->inT; a.v0 = sim->v_lazy ? sim->v0 : nullptr; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
     a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
     a.olog = sim->olog_t; a.olog_stride = sim->olog_stride; a.olog_rows = sim->B;
     const int grid = std::min(bs->n_sm, a.items);
@@ -939,10 +945,14 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
                                         : (sim->neg_mode ? batched_tick_kernel<int, 1> : batched_tick_kernel<int, 0>);
     kern<<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
+    sim->v_lazy = 0;  // this tick wrote V and the spike masks
     return cudaGetLastError();
 }
 
-cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
+// V <- v0 and no spikes: materialised only when something reads the state
+// before the first tick after a reset (that tick reads v0 itself).
+static cudaError_t batched_materialize(ranc_sim *sim) {
+    if (!sim->v_lazy) return cudaSuccess;
     const long long total = (long long)sim->T * sim->C * 4 * sim->N * (sim->vmode == kVInt32 ? 8 : 4);  // 16-byte vectors
     if (sim->vmode == kVHalf)
         batched_reset_v<__half><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((__half *)sim->V, sim->v0, sim->C, sim->N, total);
@@ -953,8 +963,33 @@ cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
     sim->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(sim->ring, 0, (size_t)sim->T * sim->C * kRows * sim->A * 16, sim->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(sim->spk, 0, (size_t)sim->T * sim->C * 4 * sim->N * 4, sim->stream)) != cudaSuccess) return e;
+    sim->v_lazy = 0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
+    // Potentials and spike masks: the first tick reads v0 instead of V and
+    // writes every spike mask, so nothing is written here.
+    sim->v_lazy = 1;
+    // Scheduler rows.  After normal stepping up to tick t, a row can hold
+    // bits only if a delivery of tick t' < t targets a tick >= t, i.e. rows
+    // t .. t + max_delay - 1 (mod 16): every other row was cleared when it was
+    // read.  Only those rows are cleared, unless the rows may hold anything
+    // (new handle, imported state, failed kernel).
+    const size_t row = (size_t)sim->A * 16, block = row * kRows;  // bytes per row, per (tile, core)
+    cudaError_t e;
+    if (sim->ring_all_dirty || sim->max_delay >= kRows) {
+        if ((e = cudaMemsetAsync(sim->ring, 0, (size_t)sim->T * sim->C * block, sim->stream)) != cudaSuccess) return e;
+        sim->ring_all_dirty = 0;
+    } else if (sim->max_delay > 0 && sim->tick > 0) {
+        const int r0 = (int)(sim->tick & (kRows - 1)), n1 = std::min(sim->max_delay, kRows - r0), n2 = sim->max_delay - n1;
+        uint8_t *base = reinterpret_cast<uint8_t *>(sim->ring);
+        if ((e = cudaMemset2DAsync(base + r0 * row, block, 0, n1 * row, (size_t)sim->T * sim->C, sim->stream)) != cudaSuccess)
+            return e;
+        if (n2 > 0 && (e = cudaMemset2DAsync(base, block, 0, n2 * row, (size_t)sim->T * sim->C, sim->stream)) != cudaSuccess)
+            return e;
+    }
     if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B_pad * sim->n_outputs * 4, sim->stream)) != cudaSuccess) return e;
     if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -979,20 +1014,9 @@ cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n
     return cudaGetLastError();
 }
 
-// Input lines of the tick about to be simulated into its scheduler row (all
-// deliveries for that row happened in earlier ticks, so the row is final).
-cudaError_t batched_inject(ranc_sim *sim) {
-    Batched *bs = B_of(sim);
-    if (!bs->inT || bs->n_pairs == 0 || sim->tick >= sim->in_ticks) return cudaSuccess;
-    const long long total = (long long)sim->T * bs->n_pairs;
-    inject_inputs<<<(unsigned)grid_for(total), 256, 0, sim->stream>>>(
-        bs->inT, sim->in_ticks, bs->Lpad, (int)sim->tick, (int)sim->tick + 1, sim->T, sim->C, sim->A, bs->inj_ca,
-        bs->inj_ptr, bs->fin_line, bs->n_pairs, reinterpret_cast<uint4 *>(sim->ring));
-    sim->launches++;
-    return cudaGetLastError();
-}
-
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk, uint32_t *ring) {
+    cudaError_t e0 = batched_materialize(sim);
+    if (e0 != cudaSuccess) return e0;
     const long long total = (long long)nb * sim->C * sim->N + (long long)nb * sim->C * (sim->N / 32) +
                             (ring ? (long long)nb * sim->C * kRows * (sim->A / 32) : 0);
     if (sim->vmode == kVHalf)
@@ -1009,6 +1033,8 @@ cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_
 }
 
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *spk, const uint32_t *ring) {
+    sim->v_lazy = 0;          // V and the spike masks are overwritten
+    sim->ring_all_dirty = 1;  // any row may hold deliveries now
     const long long total = (long long)sim->B * sim->C * sim->N + (long long)sim->T * sim->C * 4 * sim->N +
                             (long long)sim->T * sim->C * kRows * sim->A * 4;
     if (sim->vmode == kVHalf)
@@ -1078,7 +1104,7 @@ cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, u
 void batched_teardown(ranc_sim *sim) {
     Batched *bs = B_of(sim);
     if (!bs) return;
-    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT, bs->inj_ca, bs->inj_ptr};
+    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete bs;

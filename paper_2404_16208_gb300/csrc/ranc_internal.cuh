@@ -93,6 +93,9 @@ struct ranc_sim {
     int C = 0, A = 0, N = 0, K = 0, B = 0, path = 0, neg_mode = 0;
     int grid_w = 0, grid_h = 0, n_inputs = 0, n_outputs = 0, in_words = 0, weight_bits = 0;
     int B_pad = 0, T = 0, vmode = 0;    // batched path: padded batch, tiles, potential storage (kVInt32 ...)
+    int v_lazy = 0;                     // batched: V and spike masks are the reset values, not yet written
+    int ring_all_dirty = 1;             // batched: any scheduler row may hold bits (full clear on reset)
+    int max_delay = 15;                 // batched: largest core-to-core delay of the network
     cudaStream_t stream = nullptr;
     int device = 0;
 
@@ -166,7 +169,6 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
 cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
-cudaError_t batched_inject(ranc_sim *sim);
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, uint32_t *spk_canon,
                                   uint32_t *ring_canon);
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *spk_canon,
