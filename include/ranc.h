@@ -242,8 +242,21 @@ int ranc_load_state(ranc_sim *sim, const void *buf, size_t n);
 int ranc_set_kernel_timing(ranc_sim *sim, int32_t enable);
 int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
 
-/* Number of kernels this handle has launched since ranc_create. */
+/* Number of kernels this handle has launched since ranc_create (kernels of a
+ * replayed window graph, see ranc_run_samples, included). */
 int ranc_launch_count(const ranc_sim *sim, int64_t *launches);
+
+/* CUDA graphs of ranc_run_samples.  On the batched path with device buffers
+ * (RANC_MEM_DEVICE, kernel timing off) the launch sequence of a call (per group
+ * of `batch` samples: reset, input transposition, `window` tick kernels, output
+ * copy) depends only on its arguments, so the first call records it as a CUDA
+ * graph and later calls with the same inputs, counts, n_samples, t_in and
+ * window replay it with one graph launch (a reset that depends on the handle's
+ * state runs before it).  The paper launches its kernels one by one from the
+ * host every tick (Sec. III); this is the library's own addition.  *captures
+ * receives the number of recordings and *replays the number of calls served
+ * by a replay.  Errors: RANC_EINVAL if a pointer is NULL. */
+int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays);
 
 /* How the handle stores the membrane potentials in device memory.  The paper
  * makes the potential's bit width a configuration parameter (Sec. III and

@@ -737,6 +737,99 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
     return RANC_OK;
 }
 
+// Groups of B samples back to back: (reset, except before the first group),
+// inputs, `window` ticks, output counts.  Device buffers only.
+static int run_groups_device(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window, uint32_t *counts) {
+    const size_t per = (size_t)t_in * sim->in_words;
+    for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
+        const int ns = std::min(sim->B, n_samples - s0);
+        int rc = s0 > 0 ? reset_state(sim, false) : RANC_OK;
+        if (rc) return rc;
+        rc = load_inputs_dev(sim, t_in > 0 ? inputs + (size_t)s0 * per : nullptr, ns, t_in);
+        if (rc) return rc;
+        rc = step_ticks(sim, window);
+        if (rc) return rc;
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts + (size_t)s0 * sim->n_outputs, sim->out, (size_t)ns * sim->n_outputs * 4,
+                                          cudaMemcpyDeviceToDevice, sim->stream));
+    }
+    return RANC_OK;
+}
+
+// Batched path, device buffers: every call with the same arguments issues the
+// same launch sequence, so it is recorded once as a CUDA graph (on a private
+// stream) and replayed by one graph launch afterwards.  The first reset
+// depends on the handle's state (which scheduler rows may hold deliveries) and
+// runs before the graph; everything after it is fixed by the arguments.
+static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window, uint32_t *counts) {
+    const void *inT = nullptr;
+    cudaError_t e = batched_reserve_inputs(sim, t_in, &inT);  // may allocate: never inside the recording
+    if (e == cudaErrorMemoryAllocation) return fail(sim, RANC_ENOMEM, "batched input buffers");
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "batched input buffers: %s", cudaGetErrorString(e));
+    int rc = reset_state(sim, false);
+    if (rc) return rc;
+    ranc_sim::WinKey key;
+    key.inputs = inputs;
+    key.counts = counts;
+    key.inT = inT;
+    key.n_samples = n_samples;
+    key.t_in = t_in;
+    key.window = window;
+    if (sim->win_exec && key == sim->win_key) {
+        // Host bookkeeping of the recorded sequence, then one launch.
+        sim->launches += sim->win_launches;
+        sim->ticks_total += sim->win_ticks;
+        sim->tick = sim->win_tick_after;
+        sim->v_lazy = 0;
+        CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
+        ++sim->graph_replays;
+        return RANC_OK;
+    }
+    if (sim->win_exec) {
+        cudaGraphExecDestroy(sim->win_exec);
+        sim->win_exec = nullptr;
+    }
+    if (!sim->cap_stream) CUDA_OR_FAIL(sim, cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking));
+    // The recording reads no device state and the graph runs on the handle's
+    // stream, after everything already queued there.
+    const cudaStream_t stream = sim->stream;
+    const long long l0 = sim->launches;
+    const unsigned long long t0 = sim->ticks_total;
+    sim->stream = sim->cap_stream;
+    e = cudaStreamBeginCapture(sim->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        sim->stream = stream;
+        return fail(sim, RANC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    rc = run_groups_device(sim, inputs, n_samples, t_in, window, counts);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(sim->stream, &graph);
+    sim->stream = stream;
+    if (rc || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : fail(sim, RANC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&sim->win_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        sim->win_exec = nullptr;
+        return fail(sim, RANC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    sim->win_key = key;
+    sim->win_launches = sim->launches - l0;
+    sim->win_ticks = sim->ticks_total - t0;
+    sim->win_tick_after = sim->tick;
+    ++sim->graph_captures;
+    CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
+    return RANC_OK;
+}
+
+extern "C" int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays) {
+    if (!sim || !captures || !replays) return RANC_EINVAL;
+    *captures = sim->graph_captures;
+    *replays = sim->graph_replays;
+    return RANC_OK;
+}
+
 extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in,
                                 int32_t window, uint32_t *counts, int32_t mem) {
     CHECK_LIVE(sim);
@@ -748,6 +841,13 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
     if (sim->path == RANC_PATH_PLAIN) {
         int rc = run_windows_persistent(sim, inputs, n_samples, t_in, window, counts, mem);
         if (rc != RANC_ENOTSUP) return rc;  // otherwise fall through to per-tick launches
+    }
+    if (sim->path == RANC_PATH_BATCHED && mem == RANC_MEM_DEVICE && !sim->timing) {
+        int rc = run_samples_graph(sim, inputs, n_samples, t_in, window, counts);
+        sim->in_override = nullptr;
+        sim->n_valid = sim->B;
+        sim->in_ticks = 0;  // the window inputs are not kept as the handle's schedule
+        return rc;
     }
     for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
         const int ns = std::min(sim->B, n_samples - s0);
@@ -1007,6 +1107,8 @@ extern "C" int ranc_potential_format(const ranc_sim *sim, int32_t *format) {
 extern "C" void ranc_destroy(ranc_sim *sim) {
     if (!sim) return;
     cudaStreamSynchronize(sim->stream);
+    if (sim->win_exec) cudaGraphExecDestroy(sim->win_exec);
+    if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
     free_all(sim);
     delete sim;
 }

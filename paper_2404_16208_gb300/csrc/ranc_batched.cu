@@ -995,7 +995,9 @@ cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
     return cudaSuccess;
 }
 
-cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks) {
+// Makes the transposed-input buffer hold n_ticks ticks (may synchronise the
+// stream and reallocate); *buffer receives its address.
+cudaError_t batched_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer) {
     Batched *bs = B_of(sim);
     const size_t need = (size_t)sim->T * n_ticks * bs->Lpad;  // uint4 units
     if (need > bs->inT_cap) {
@@ -1007,6 +1009,14 @@ cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n
         if (dev_alloc((void **)&bs->inT, need * 16) != cudaSuccess) return cudaErrorMemoryAllocation;
         bs->inT_cap = need;
     }
+    if (buffer) *buffer = bs->inT;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks) {
+    Batched *bs = B_of(sim);
+    cudaError_t er = batched_reserve_inputs(sim, n_ticks, nullptr);
+    if (er != cudaSuccess) return er;
     const long long threads = (long long)sim->T * n_ticks * sim->in_words * 4 * 32;
     transpose_inputs<<<(unsigned)((threads + 255) / 256), 256, 0, sim->stream>>>(dev_bits, n_samples, n_ticks,
                                                                                 sim->in_words, sim->T, (uint32_t *)bs->inT);

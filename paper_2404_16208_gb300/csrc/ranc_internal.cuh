@@ -143,6 +143,23 @@ struct ranc_sim {
     double timed_ms = 0.0;
     long long timed_launches = 0;
 
+    // run_samples on the batched path with device buffers: the window sequence
+    // recorded as a CUDA graph, replayed while its arguments stay the same
+    cudaGraphExec_t win_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the sequence is recorded on
+    struct WinKey {
+        const void *inputs = nullptr, *counts = nullptr, *inT = nullptr;
+        int n_samples = -1, t_in = -1, window = -1;
+        bool operator==(const WinKey &o) const {
+            return inputs == o.inputs && counts == o.counts && inT == o.inT && n_samples == o.n_samples &&
+                   t_in == o.t_in && window == o.window;
+        }
+    } win_key;
+    long long win_launches = 0;          // kernels in the recorded sequence
+    unsigned long long win_ticks = 0;    // sample ticks it advances
+    long long win_tick_after = 0;        // tick counter after it
+    long long graph_captures = 0, graph_replays = 0;
+
     int sticky = 0;
     int stall_test = 0;                  // RANC_TEST_STALL_WAIT (failure-detection tests)
     std::string last_error;
@@ -174,5 +191,6 @@ cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, u
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint32_t *spk_canon,
                                   const uint32_t *ring_canon);
 cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, uint32_t *spk_host);
+cudaError_t batched_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer);
 void batched_teardown(ranc_sim *sim);
 }  // namespace ranc
