@@ -34,8 +34,13 @@ struct PlainArgs {
     int n_valid;                 // samples b < n_valid receive inputs
     int in_words, in_ticks, n_out, neg_mode;
     long long tick;              // tick being simulated (counted from reset)
-    const uint32_t *xbarT;       // [C][N][AW]   crossbar bits, one row of axon bits per neuron
-    const uint32_t *tmask;       // [C][K][AW]   axons of each type
+    // The plain kernels integrate over the axons of each core sorted by type
+    // (then by index): position p holds axon axperm[c][p], so most 32-axon
+    // words hold one type.  Scheduler rows, inputs and packets keep the
+    // original axon numbers; a tick gathers its active axons into this order.
+    const uint32_t *xbarT;       // [C][AW][N]   crossbar bits in sorted order: word w of neuron n's row at [c][w][n]
+    const uint32_t *tmask;       // [C][K][AW]   positions (sorted order) of each type
+    const uint16_t *axperm;      // [C][A]       axon at each sorted position
     const int16_t *wnk;          // [C][N][8]    weight per (neuron, type)
     const int4 *prm;             // [C][N]       {leak, pos_thr, neg_thr, reset}
     const uint2 *dst;            // [C][N]       resolved destination
@@ -77,7 +82,6 @@ struct BatchedArgs {
     const int *in_ptr, *in_line, *in_axon;   // per-core (line, axon) lists
     const uint32_t *inT;         // [T][in_ticks][n_inputs][4] sample-minor input bits
     int n_inputs;
-    const uint32_t *xbarT;       // [C][N][AW] (synaptic-event count)
     void *V;                     // [T][C][N/32][kTileS][32] int16 or int32
     uint32_t *ring;              // [T][C][kRows][A][4] sample-minor scheduler rows
     uint32_t *out;               // [B_pad][n_out]
@@ -101,6 +105,7 @@ struct ranc_sim {
 
     // constant network arrays (device)
     uint32_t *xbarT = nullptr, *tmask = nullptr;
+    uint16_t *axperm = nullptr;         // plain: [C][A] axon at each type-sorted position
     int16_t *wnk = nullptr;
     int4 *prm = nullptr;
     uint2 *dst = nullptr;

@@ -23,10 +23,67 @@
 
 namespace ranc {
 
+// Weight of type k from a neuron's 8 packed int16 weights (selects, no
+// indexed register array).
+__device__ __forceinline__ int weight_of(const uint32_t (&wr)[4], int k) {
+    const uint32_t lo = (k & 2) ? wr[1] : wr[0], hi = (k & 2) ? wr[3] : wr[2];
+    return (int)(int16_t)(((k & 4) ? hi : lo) >> (16 * (k & 1)));
+}
+
+// Active axons of `ncores` cores in type-sorted order: bit p of core j's
+// sp words is bit perm[j * A + p] of its s words (original order).  Thread t
+// of nt (a multiple of 32) takes positions t, t + nt, ...; the lanes of a warp
+// hold 32 consecutive positions of one core (A is a multiple of 32), so one
+// ballot builds a word.
+__device__ __forceinline__ void gather_sorted(const uint32_t *s, const uint16_t *perm, int A, int AW, int ncores,
+                                              uint32_t *sp, int t, int nt) {
+    for (int i = t; i < ncores * A; i += nt) {
+        const int j = i / A, ia = perm[i];
+        const unsigned word = __ballot_sync(0xffffffffu, (s[j * AW + (ia >> 5)] >> (ia & 31)) & 1u);
+        if ((i & 31) == 0) sp[i >> 5] = word;  // = sp[j * AW + (i % A) / 32]
+    }
+}
+
+// dV and the synaptic-event count of one neuron over the sorted active axons
+// sp: a word holding one type (wt[w] = type) costs one popc; a word at a type
+// boundary (wt[w] < 0) one popc per type.
+__device__ __forceinline__ int integrate_sorted(const uint32_t *sp, const uint32_t *xr, int N, const uint32_t *tm,
+                                                const int8_t *wt, int AW, int K, const uint32_t (&wr)[4], uint32_t &syn) {
+    int dv = 0;
+    for (int w = 0; w < AW; ++w) {
+        const uint32_t sw = sp[w];
+        if (sw == 0u) continue;  // uniform across the core's threads
+        const uint32_t x = sw & xr[(size_t)w * N];
+        const int pt = wt[w];
+        if (pt >= 0) {
+            const uint32_t c1 = __popc(x);
+            syn += c1;
+            dv += weight_of(wr, pt) * (int)c1;
+        } else {
+            for (int k = 0; k < K; ++k) {
+                const uint32_t ck = __popc(x & tm[k * AW + w]);
+                syn += ck;
+                dv += weight_of(wr, k) * (int)ck;
+            }
+        }
+    }
+    return dv;
+}
+
+// wt[w] = k if word w of the sorted axons holds only type k, else -1.
+__device__ __forceinline__ int8_t word_type(const uint32_t *tm, int AW, int K, int w) {
+    for (int k = 0; k < K; ++k)
+        if (tm[k * AW + w] == 0xffffffffu) return (int8_t)k;
+    return (int8_t)-1;
+}
+
 __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
-    extern __shared__ __align__(128) uint32_t xs[];  // [N][AW] crossbar rows of this core
-    __shared__ uint32_t s[kMaxWords];                 // active axons of this tick
-    __shared__ uint32_t tm[kMaxTypes * kMaxWords];    // axon-type masks
+    extern __shared__ __align__(128) uint32_t xs[];  // [AW][N] crossbar of this core (sorted axons), word-major
+    __shared__ uint32_t s[kMaxWords];                 // active axons of this tick (original order)
+    __shared__ uint32_t sp[kMaxWords];                // the same, type-sorted order
+    __shared__ uint32_t tm[kMaxTypes * kMaxWords];    // axon-type masks (sorted order)
+    __shared__ uint16_t perm[kMaxWords * 32];         // axon at each sorted position
+    __shared__ int8_t wt[kMaxWords];                  // type of each sorted word, or -1
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t red[4];
 
@@ -48,8 +105,10 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
         row[n] = 0u;
     }
     for (int i = n; i < K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c * K * AW + i];
+    for (int i = n; i < a.A; i += blockDim.x) perm[i] = a.axperm[(size_t)c * a.A + i];
     if (n < 4) red[n] = 0u;
     __syncthreads();
+    if (n < AW) wt[n] = word_type(tm, AW, K, n);
 
     // Input lines of this tick (reading: input delay 0).
     if (b < a.n_valid && a.tick < a.in_ticks) {
@@ -80,27 +139,15 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
         return;
     }
 
-    // Crossbar integration: count active, connected axons per type.
-    const uint32_t *xr = xs + (size_t)n * AW;
-    uint32_t cntk[kMaxTypes];
-#pragma unroll
-    for (int k = 0; k < kMaxTypes; ++k) cntk[k] = 0u;
-    uint32_t syn = 0u;
-    for (int w = 0; w < AW; ++w) {
-        const uint32_t sw = s[w];
-        if (sw == 0u) continue;  // uniform across the CTA
-        const uint32_t x = sw & xr[w];
-        syn += __popc(x);
-#pragma unroll
-        for (int k = 0; k < kMaxTypes; ++k)
-            if (k < K) cntk[k] += __popc(x & tm[k * AW + w]);
-    }
+    // Crossbar integration over the type-sorted active axons (word w of
+    // neuron n's row at xs[w * N + n]: a warp reads consecutive words, free of
+    // bank conflicts); the per-type counts sum to the synaptic events.
+    gather_sorted(s, perm, a.A, AW, 1, sp, n, blockDim.x);
+    __syncthreads();
     const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
     const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
-    int dv = 0;
-#pragma unroll
-    for (int k = 0; k < kMaxTypes; ++k)
-        if (k < K) dv += (int)(int16_t)(wr[k >> 1] >> (16 * (k & 1))) * (int)cntk[k];
+    uint32_t syn = 0u;
+    const int dv = integrate_sorted(sp, xs + n, N, tm, wt, AW, K, wr, syn);
 
     // Leak, thresholds, reset.
     const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
@@ -163,28 +210,28 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     return v;
 }
 
-// Grid-wide barrier over all CTAs of a cooperative launch.  bar[0] counts
-// arrivals, bar[1] is the generation.  Returns false if the wait gave up.
+// Grid-wide barrier over all CTAs of a cooperative launch: bar[0] counts
+// arrivals without ever being reset (barrier k completes when it reaches
+// k * nblocks).  Thread 0 of each CTA arrives with one acquire-release atomic
+// (after the CTA barrier, so it publishes the whole CTA's writes) and, unless
+// it was the last to arrive, polls with acquire loads.  Returns false if the
+// wait gave up.
 __device__ bool grid_sync(unsigned *bar, unsigned nblocks, unsigned &gen, int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
-        __threadfence();
-        const unsigned g = gen;
-        if (atomicAdd(&bar[0], 1u) + 1u == nblocks) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicExch(&bar[1], g + 1u);
-        } else if (ld_acquire_u32(&bar[1]) == g) {
+        const unsigned target = (gen + 1u) * nblocks;
+        unsigned v;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+        if (v + 1u != target && (int)(ld_acquire_u32(bar) - target) < 0) {
             const unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(&bar[1]) == g) {
+            while ((int)(ld_acquire_u32(bar) - target) < 0) {
                 if (global_ns() - t0 > kWaitLimitNs) {
                     ok = false;
                     break;
                 }
             }
         }
-        __threadfence();
         *s_ok = ok ? 1 : 0;
     }
     __syncthreads();
@@ -204,10 +251,13 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     const int c_first = grp * G, ncores = min(G, C - c_first);
     const int c = c_first + cg;
     const bool has_core = cg < ncores;
-    uint32_t *xs = sm;                         // [ncores][N][AW]
-    uint32_t *tm = xs + (size_t)G * N * AW;    // [ncores][K][AW]
-    uint32_t *sb = tm + (size_t)G * K * AW;    // [ncores][AW] active axons of this tick
-    uint32_t *inb = sb + (size_t)G * AW;       // [t_in][in_words] inputs of this CTA's sample
+    uint32_t *xs = sm;                         // [ncores][AW][N] (word-major, type-sorted axons)
+    uint32_t *tm = xs + (size_t)G * N * AW;    // [ncores][K][AW] (sorted axons)
+    uint32_t *sb = tm + (size_t)G * K * AW;    // [ncores][AW] active axons of this tick (original order)
+    uint32_t *spb = sb + (size_t)G * AW;       // [ncores][AW] the same in sorted order
+    uint16_t *perm = reinterpret_cast<uint16_t *>(spb + (size_t)G * AW);  // [ncores][A] axon at each sorted position
+    int8_t *wt = reinterpret_cast<int8_t *>(perm + (size_t)G * a.A);      // [ncores][AW] type of each sorted word or -1
+    uint32_t *inb = reinterpret_cast<uint32_t *>(wt + (((size_t)G * AW + 15) & ~(size_t)15));  // [t_in][in_words] inputs
     const unsigned nblocks = gridDim.x;
     unsigned gen = 0;
 
@@ -219,6 +269,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
         bulk_g2s(xs, a.xbarT + (size_t)c_first * N * AW, xbytes, &bar);
     }
     for (int i = tid; i < ncores * K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c_first * K * AW + i];
+    for (int i = tid; i < ncores * a.A; i += blockDim.x) perm[i] = a.axperm[(size_t)c_first * a.A + i];
     int lam = 0, pth = 0, nth = 0, rst = 0, v0 = 0;
     uint32_t wr[4] = {0u, 0u, 0u, 0u};
     uint2 dd = make_uint2(0u, 0u);
@@ -238,6 +289,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     }
     if (tid < kMaxWindowCores * 4) red[tid / 4][tid % 4] = 0u;
     __syncthreads();
+    for (int i = tid; i < ncores * AW; i += blockDim.x) wt[i] = word_type(tm + (size_t)(i / AW) * K * AW, AW, K, i % AW);
     const bool ok0 = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok0)) {
         if (tid == 0) atomicExch(a.err, kErrTimeout);
@@ -248,6 +300,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     const int ipw = w.t_in * a.in_words;
     const int ip0 = a.in_ptr[c_first], ip1 = a.in_ptr[c_first + ncores];
     uint32_t n_sp = 0, n_pk = 0, n_ou = 0, n_syn = 0;
+    uint32_t oc = 0u;  // this neuron's output-bus events in the current window
     int V = v0;
     const int n_windows = (w.n_samples + a.B - 1) / a.B;
     for (int win = 0; win < n_windows; ++win) {
@@ -288,28 +341,13 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                 }
                 __syncthreads();
             }
+            gather_sorted(sb, perm, a.A, AW, ncores, spb, tid, blockDim.x);
+            __syncthreads();
             bool fire = false;
             if (has_core) {
-                const uint32_t *xr = xs + ((size_t)cg * N + n) * AW;
-                const uint32_t *sc = sb + cg * AW;
-                const uint32_t *tc = tm + (size_t)cg * K * AW;
-                uint32_t cntk[kMaxTypes];
-#pragma unroll
-                for (int k = 0; k < kMaxTypes; ++k) cntk[k] = 0u;
                 uint32_t syn = 0u;
-                for (int wd = 0; wd < AW; ++wd) {
-                    const uint32_t sw = sc[wd];
-                    if (sw == 0u) continue;
-                    const uint32_t x = sw & xr[wd];
-                    syn += __popc(x);
-#pragma unroll
-                    for (int k = 0; k < kMaxTypes; ++k)
-                        if (k < K) cntk[k] += __popc(x & tc[k * AW + wd]);
-                }
-                int dv = 0;
-#pragma unroll
-                for (int k = 0; k < kMaxTypes; ++k)
-                    if (k < K) dv += (int)(int16_t)(wr[k >> 1] >> (16 * (k & 1))) * (int)cntk[k];
+                const int dv = integrate_sorted(spb + cg * AW, xs + (size_t)cg * AW * N + n, N, tm + (size_t)cg * K * AW,
+                                                wt + cg * AW, AW, K, wr, syn);
                 int x = V + dv + lam;
                 fire = x >= pth;
                 if (fire)
@@ -328,7 +366,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                         atomicOr(a.ring + (((size_t)b * C + dd.x) * kRows + rr) * AW + (ax >> 5), 1u << (ax & 31));
                         if (valid) ++n_pk;
                     } else if (kind == RANC_DEST_OUTPUT) {
-                        atomicAdd(a.out + (size_t)b * a.n_out + dd.x, 1u);
+                        ++oc;  // added to the output bus once, at the window's last tick
                         if (valid) {
                             ++n_ou;
                             if (w.olog)
@@ -336,6 +374,10 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                         }
                     }
                 }
+            }
+            if (t == w.window - 1 && oc) {
+                atomicAdd(a.out + (size_t)b * a.n_out + dd.x, oc);
+                oc = 0u;
             }
             const unsigned fm = __ballot_sync(0xffffffffu, fire);
             if (has_core && lane == 0) a.spk[((size_t)b * C + c) * a.NW + n / 32] = fm;
@@ -375,8 +417,9 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
 // otherwise, so the caller can use the per-tick launches instead.
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     const int threads = w.G * w.p.N;
-    const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + (size_t)w.G * w.p.AW +
-                         (w.stream ? 0 : (size_t)w.t_in * w.p.in_words)) * 4;
+    const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + 2 * (size_t)w.G * w.p.AW) * 4 +
+                        (size_t)w.G * w.p.A * 2 + (((size_t)w.G * w.p.AW + 15) & ~(size_t)15) +
+                        (w.stream ? 0 : (size_t)w.t_in * w.p.in_words) * 4;
     cudaError_t e = raise_smem_limit((const void *)plain_window_kernel, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 0, per_sm = 0;
