@@ -154,7 +154,7 @@ bool validate(const ranc_desc *d, int batch, int path, std::vector<int> &core_at
 }
 
 void free_all(ranc_sim *s) {
-    void *ptrs[] = {s->xbarT, s->tmask, s->axperm, s->wnk, s->prm, s->dst, s->in_ptr, s->in_line, s->in_axon, s->v0,
+    void *ptrs[] = {s->xbarT, s->wtype, s->axperm, s->wnk, s->prm, s->dst, s->in_ptr, s->in_line, s->in_axon, s->v0,
                     s->V, s->ring, s->spk, s->out, s->cnt, s->inputs, s->err, s->digest, s->stage,
                     s->gbar, s->counts_dev, s->olog_dev};
     for (void *p : ptrs)
@@ -229,7 +229,7 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
             a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
             a.B = sim->B; a.n_valid = sim->n_valid; a.in_words = sim->in_words; a.in_ticks = sim->in_ticks;
             a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = sim->tick;
-            a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.axperm = sim->axperm; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+            a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
             a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon;
             a.inputs = sim->in_override ? sim->in_override : sim->inputs;
             a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
@@ -435,25 +435,39 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     if (e != cudaSuccess) return abort_create(RANC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
 
     // Host-side layout of the constant arrays.
-    std::vector<uint32_t> xbarT((size_t)C * N * AW, 0u), tmask((size_t)C * K * AW, 0u);
-    std::vector<uint16_t> axperm((size_t)C * A);
+    // Type-sorted axon order of the plain kernels (see PlainArgs::axperm):
+    // every type starts at a word boundary, so a core needs sum_k ceil(n_k / 32)
+    // words; SW is the largest over the cores.
+    int SW = 1;
+    for (int c = 0; c < C; c++) {
+        std::vector<int> nk(K, 0);
+        for (int a = 0; a < A; a++) nk[d->axon_type[(size_t)c * A + a]]++;
+        int words = 0;
+        for (int k = 0; k < K; k++) words += (nk[k] + 31) / 32;
+        SW = std::max(SW, words);
+    }
+    sim->SW = SW;
+    std::vector<uint32_t> xbarT((size_t)C * SW * N, 0u);
+    std::vector<int8_t> wtype((size_t)C * SW, (int8_t)-1);
+    std::vector<uint16_t> axperm((size_t)C * SW * 32, (uint16_t)0xFFFF);
     std::vector<int16_t> wnk((size_t)C * N * kMaxTypes, 0);
     std::vector<int4> prm((size_t)C * N);
     std::vector<uint2> dst((size_t)C * N);
     const int NWd = N / 32;
     for (int c = 0; c < C; c++) {
-        // Axons sorted by type, then by index (see PlainArgs::axperm).
-        uint16_t *ord = axperm.data() + (size_t)c * A;
-        for (int a = 0; a < A; a++) ord[a] = (uint16_t)a;
-        std::stable_sort(ord, ord + A, [&](uint16_t x, uint16_t y) {
-            return d->axon_type[(size_t)c * A + x] < d->axon_type[(size_t)c * A + y];
-        });
-        for (int p = 0; p < A; p++) {
-            const int a = ord[p];
-            const uint32_t *src = d->crossbar + ((size_t)c * A + a) * NWd;
-            for (int n = 0; n < N; n++)
-                if ((src[n >> 5] >> (n & 31)) & 1u) xbarT[((size_t)c * AW + (p >> 5)) * N + n] |= 1u << (p & 31);
-            tmask[((size_t)c * K + d->axon_type[(size_t)c * A + a]) * AW + (p >> 5)] |= 1u << (p & 31);
+        int p = 0;  // next sorted position
+        for (int k = 0; k < K; k++) {
+            const int p0 = p;
+            for (int a = 0; a < A; a++) {
+                if (d->axon_type[(size_t)c * A + a] != k) continue;
+                axperm[(size_t)c * SW * 32 + p] = (uint16_t)a;
+                const uint32_t *src = d->crossbar + ((size_t)c * A + a) * NWd;
+                for (int n = 0; n < N; n++)
+                    if ((src[n >> 5] >> (n & 31)) & 1u) xbarT[((size_t)c * SW + (p >> 5)) * N + n] |= 1u << (p & 31);
+                ++p;
+            }
+            for (int w = p0 / 32; w < (p + 31) / 32; w++) wtype[(size_t)c * SW + w] = (int8_t)k;
+            p = (p + 31) & ~31;
         }
         for (int n = 0; n < N; n++) {
             const size_t i = (size_t)c * N + n;
@@ -486,7 +500,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     }
     std::vector<int> v0(d->v0, d->v0 + (size_t)C * N);
 
-    if (upload(&sim->xbarT, xbarT) != cudaSuccess || upload(&sim->tmask, tmask) != cudaSuccess ||
+    if (upload(&sim->xbarT, xbarT) != cudaSuccess || upload(&sim->wtype, wtype) != cudaSuccess ||
         upload(&sim->axperm, axperm) != cudaSuccess ||
         upload(&sim->wnk, wnk) != cudaSuccess || upload(&sim->prm, prm) != cudaSuccess ||
         upload(&sim->dst, dst) != cudaSuccess || upload(&sim->in_ptr, in_ptr) != cudaSuccess ||
@@ -504,7 +518,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
             dmalloc(&sim->cnt, (size_t)batch * C * 4) != cudaSuccess || dmalloc(&sim->gbar, 2) != cudaSuccess)
             return abort_create(RANC_ENOMEM, "device allocation of the state arrays failed");
         sim->cnt_len = (size_t)batch * C * 4;
-        e = plain_setup_kernel_attrs(N, AW);
+        e = plain_setup_kernel_attrs(N, SW);
         if (e != cudaSuccess) return abort_create(RANC_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     } else {
         e = batched_setup(sim, d, why);
@@ -708,7 +722,7 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
     a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
     a.B = sim->B; a.n_valid = sim->B; a.in_words = sim->in_words; a.in_ticks = t_in;
     a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = 0;
-    a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.axperm = sim->axperm; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+    a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -904,7 +918,7 @@ static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in
     a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
     a.B = sim->B; a.n_valid = sim->B; a.in_words = sim->in_words; a.in_ticks = n_in;
     a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = 0;
-    a.xbarT = sim->xbarT; a.tmask = sim->tmask; a.axperm = sim->axperm; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+    a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

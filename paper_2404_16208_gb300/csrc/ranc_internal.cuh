@@ -14,6 +14,7 @@ namespace ranc {
 constexpr int kRows = RANC_ROWS;     // scheduler rows (Sec. III-E); delays 1..15
 constexpr int kMaxTypes = 8;         // weight slots per neuron
 constexpr int kMaxWords = 32;        // axons/32 and neurons/32 upper bound (1024)
+constexpr int kMaxSortedWords = kMaxWords + kMaxTypes;  // words of the type-sorted axon order (each type word-aligned)
 constexpr int kTileS = 128;          // samples per tensor-core tile (batched path)
 // Storage of the batched path's potentials (values of RANC_POTENTIAL_*).
 constexpr int kVInt32 = 0, kVInt16 = 1, kVHalf = 2;
@@ -31,16 +32,18 @@ __host__ __device__ inline uint32_t dest_kind(uint2 d) { return d.y >> 24; }
 // Per-launch parameters of the plain (one thread per neuron) tick kernel.
 struct PlainArgs {
     int C, A, N, K, AW, NW, B;   // cores, axons, neurons, types, A/32, N/32, batch
+    int SW;                      // words of the type-sorted axon order (same for every core)
     int n_valid;                 // samples b < n_valid receive inputs
     int in_words, in_ticks, n_out, neg_mode;
     long long tick;              // tick being simulated (counted from reset)
     // The plain kernels integrate over the axons of each core sorted by type
-    // (then by index): position p holds axon axperm[c][p], so most 32-axon
-    // words hold one type.  Scheduler rows, inputs and packets keep the
+    // (then by index), every type starting at a 32-position boundary: position
+    // p holds axon axperm[c][p] (0xFFFF: none), and word w holds only type
+    // wtype[c][w] (-1: no axon).  Scheduler rows, inputs and packets keep the
     // original axon numbers; a tick gathers its active axons into this order.
-    const uint32_t *xbarT;       // [C][AW][N]   crossbar bits in sorted order: word w of neuron n's row at [c][w][n]
-    const uint32_t *tmask;       // [C][K][AW]   positions (sorted order) of each type
-    const uint16_t *axperm;      // [C][A]       axon at each sorted position
+    const uint32_t *xbarT;       // [C][SW][N]   crossbar bits in sorted order: word w of neuron n's row at [c][w][n]
+    const int8_t *wtype;         // [C][SW]      type of each sorted word
+    const uint16_t *axperm;      // [C][SW*32]   axon at each sorted position
     const int16_t *wnk;          // [C][N][8]    weight per (neuron, type)
     const int4 *prm;             // [C][N]       {leak, pos_thr, neg_thr, reset}
     const uint2 *dst;            // [C][N]       resolved destination
@@ -104,8 +107,10 @@ struct ranc_sim {
     int device = 0;
 
     // constant network arrays (device)
-    uint32_t *xbarT = nullptr, *tmask = nullptr;
-    uint16_t *axperm = nullptr;         // plain: [C][A] axon at each type-sorted position
+    uint32_t *xbarT = nullptr;
+    int8_t *wtype = nullptr;            // plain: [C][SW] type of each word of the type-sorted axon order
+    uint16_t *axperm = nullptr;         // plain: [C][SW*32] axon at each type-sorted position
+    int SW = 0;                         // plain: words of that order
     int16_t *wnk = nullptr;
     int4 *prm = nullptr;
     uint2 *dst = nullptr;
@@ -182,7 +187,7 @@ namespace ranc {
 // Implemented in ranc_plain.cu
 cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s);
 cudaError_t raise_smem_limit(const void *kernel, int bytes);
-cudaError_t plain_setup_kernel_attrs(int N, int AW);
+cudaError_t plain_setup_kernel_attrs(int N, int SW);
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s);
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s);

@@ -30,73 +30,56 @@ __device__ __forceinline__ int weight_of(const uint32_t (&wr)[4], int k) {
     return (int)(int16_t)(((k & 4) ? hi : lo) >> (16 * (k & 1)));
 }
 
-// Active axons of `ncores` cores in type-sorted order: bit p of core j's
-// sp words is bit perm[j * A + p] of its s words (original order).  Thread t
-// of nt (a multiple of 32) takes positions t, t + nt, ...; the lanes of a warp
-// hold 32 consecutive positions of one core (A is a multiple of 32), so one
-// ballot builds a word.
-__device__ __forceinline__ void gather_sorted(const uint32_t *s, const uint16_t *perm, int A, int AW, int ncores,
+// Active axons of `ncores` cores in type-sorted order: bit p of core j's SW
+// sorted words is bit perm[j * SW * 32 + p] of its AW words in original order
+// (0 for a position without axon).  Thread t of nt (a multiple of 32) takes
+// positions t, t + nt, ...; the lanes of a warp hold 32 consecutive positions
+// of one word, so one ballot builds it.
+__device__ __forceinline__ void gather_sorted(const uint32_t *s, const uint16_t *perm, int AW, int SW, int ncores,
                                               uint32_t *sp, int t, int nt) {
-    for (int i = t; i < ncores * A; i += nt) {
-        const int j = i / A, ia = perm[i];
-        const unsigned word = __ballot_sync(0xffffffffu, (s[j * AW + (ia >> 5)] >> (ia & 31)) & 1u);
-        if ((i & 31) == 0) sp[i >> 5] = word;  // = sp[j * AW + (i % A) / 32]
+    const int P = SW * 32;
+    for (int i = t; i < ncores * P; i += nt) {
+        const int j = i / P, ia = perm[i];
+        const bool on = ia != 0xFFFF && ((s[j * AW + (ia >> 5)] >> (ia & 31)) & 1u);
+        const unsigned word = __ballot_sync(0xffffffffu, on);
+        if ((i & 31) == 0) sp[i >> 5] = word;
     }
 }
 
 // dV and the synaptic-event count of one neuron over the sorted active axons
-// sp: a word holding one type (wt[w] = type) costs one popc; a word at a type
-// boundary (wt[w] < 0) one popc per type.
-__device__ __forceinline__ int integrate_sorted(const uint32_t *sp, const uint32_t *xr, int N, const uint32_t *tm,
-                                                const int8_t *wt, int AW, int K, const uint32_t (&wr)[4], uint32_t &syn) {
+// sp: every sorted word holds one type, so a word costs one popc.
+__device__ __forceinline__ int integrate_sorted(const uint32_t *sp, const uint32_t *xr, int N, const int8_t *wt, int SW,
+                                                const uint32_t (&wr)[4], uint32_t &syn) {
     int dv = 0;
-    for (int w = 0; w < AW; ++w) {
+    for (int w = 0; w < SW; ++w) {
         const uint32_t sw = sp[w];
         if (sw == 0u) continue;  // uniform across the core's threads
-        const uint32_t x = sw & xr[(size_t)w * N];
-        const int pt = wt[w];
-        if (pt >= 0) {
-            const uint32_t c1 = __popc(x);
-            syn += c1;
-            dv += weight_of(wr, pt) * (int)c1;
-        } else {
-            for (int k = 0; k < K; ++k) {
-                const uint32_t ck = __popc(x & tm[k * AW + w]);
-                syn += ck;
-                dv += weight_of(wr, k) * (int)ck;
-            }
-        }
+        const uint32_t c1 = __popc(sw & xr[(size_t)w * N]);
+        syn += c1;
+        dv += weight_of(wr, wt[w]) * (int)c1;
     }
     return dv;
 }
 
-// wt[w] = k if word w of the sorted axons holds only type k, else -1.
-__device__ __forceinline__ int8_t word_type(const uint32_t *tm, int AW, int K, int w) {
-    for (int k = 0; k < K; ++k)
-        if (tm[k * AW + w] == 0xffffffffu) return (int8_t)k;
-    return (int8_t)-1;
-}
-
 __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
-    extern __shared__ __align__(128) uint32_t xs[];  // [AW][N] crossbar of this core (sorted axons), word-major
+    extern __shared__ __align__(128) uint32_t xs[];  // [SW][N] crossbar of this core (sorted axons), word-major
     __shared__ uint32_t s[kMaxWords];                 // active axons of this tick (original order)
-    __shared__ uint32_t sp[kMaxWords];                // the same, type-sorted order
-    __shared__ uint32_t tm[kMaxTypes * kMaxWords];    // axon-type masks (sorted order)
-    __shared__ uint16_t perm[kMaxWords * 32];         // axon at each sorted position
-    __shared__ int8_t wt[kMaxWords];                  // type of each sorted word, or -1
+    __shared__ uint32_t sp[kMaxSortedWords];          // the same, type-sorted order
+    __shared__ uint16_t perm[kMaxSortedWords * 32];   // axon at each sorted position
+    __shared__ int8_t wt[kMaxSortedWords];            // type of each sorted word
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t red[4];
 
     const int c = blockIdx.x, b = blockIdx.y, n = threadIdx.x;
-    const int AW = a.AW, K = a.K, N = a.N;
+    const int AW = a.AW, SW = a.SW, N = a.N;
     const int lane = n & 31, warp = n >> 5;
-    const uint32_t xbytes = (uint32_t)N * AW * 4u;
+    const uint32_t xbytes = (uint32_t)N * SW * 4u;
 
     if (n == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(&bar, xbytes);
-        bulk_g2s(xs, a.xbarT + (size_t)c * N * AW, xbytes, &bar);
+        bulk_g2s(xs, a.xbarT + (size_t)c * N * SW, xbytes, &bar);
     }
     const size_t bc = (size_t)b * a.C + c;
     uint32_t *row = a.ring + (bc * kRows + (a.tick & (kRows - 1))) * AW;
@@ -104,11 +87,10 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
         s[n] = row[n];
         row[n] = 0u;
     }
-    for (int i = n; i < K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c * K * AW + i];
-    for (int i = n; i < a.A; i += blockDim.x) perm[i] = a.axperm[(size_t)c * a.A + i];
+    for (int i = n; i < SW * 32; i += blockDim.x) perm[i] = a.axperm[(size_t)c * SW * 32 + i];
+    if (n < SW) wt[n] = a.wtype[(size_t)c * SW + n];
     if (n < 4) red[n] = 0u;
     __syncthreads();
-    if (n < AW) wt[n] = word_type(tm, AW, K, n);
 
     // Input lines of this tick (reading: input delay 0).
     if (b < a.n_valid && a.tick < a.in_ticks) {
@@ -142,12 +124,12 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
     // Crossbar integration over the type-sorted active axons (word w of
     // neuron n's row at xs[w * N + n]: a warp reads consecutive words, free of
     // bank conflicts); the per-type counts sum to the synaptic events.
-    gather_sorted(s, perm, a.A, AW, 1, sp, n, blockDim.x);
+    gather_sorted(s, perm, AW, SW, 1, sp, n, blockDim.x);
     __syncthreads();
     const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
     const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
     uint32_t syn = 0u;
-    const int dv = integrate_sorted(sp, xs + n, N, tm, wt, AW, K, wr, syn);
+    const int dv = integrate_sorted(sp, xs + n, N, wt, SW, wr, syn);
 
     // Leak, thresholds, reset.
     const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
@@ -190,7 +172,7 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
 }
 
 cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)a.N * a.AW * 4;
+    const size_t smem = (size_t)a.N * a.SW * 4;
     plain_tick_kernel<<<dim3(a.C, a.B), a.N, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -245,31 +227,30 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     __shared__ uint32_t red[kMaxWindowCores][4];
     __shared__ int s_ok;
     const PlainArgs &a = w.p;
-    const int G = w.G, N = a.N, AW = a.AW, K = a.K, C = a.C;
+    const int G = w.G, N = a.N, AW = a.AW, SW = a.SW, C = a.C;
     const int grp = blockIdx.x % w.n_groups, b = blockIdx.x / w.n_groups;
     const int tid = threadIdx.x, cg = tid / N, n = tid % N, lane = tid & 31;
     const int c_first = grp * G, ncores = min(G, C - c_first);
     const int c = c_first + cg;
     const bool has_core = cg < ncores;
-    uint32_t *xs = sm;                         // [ncores][AW][N] (word-major, type-sorted axons)
-    uint32_t *tm = xs + (size_t)G * N * AW;    // [ncores][K][AW] (sorted axons)
-    uint32_t *sb = tm + (size_t)G * K * AW;    // [ncores][AW] active axons of this tick (original order)
-    uint32_t *spb = sb + (size_t)G * AW;       // [ncores][AW] the same in sorted order
-    uint16_t *perm = reinterpret_cast<uint16_t *>(spb + (size_t)G * AW);  // [ncores][A] axon at each sorted position
-    int8_t *wt = reinterpret_cast<int8_t *>(perm + (size_t)G * a.A);      // [ncores][AW] type of each sorted word or -1
-    uint32_t *inb = reinterpret_cast<uint32_t *>(wt + (((size_t)G * AW + 15) & ~(size_t)15));  // [t_in][in_words] inputs
+    uint32_t *xs = sm;                         // [ncores][SW][N] (word-major, type-sorted axons)
+    uint32_t *sb = xs + (size_t)G * N * SW;    // [ncores][AW] active axons of this tick (original order)
+    uint32_t *spb = sb + (size_t)G * AW;       // [ncores][SW] the same in sorted order
+    uint16_t *perm = reinterpret_cast<uint16_t *>(spb + (size_t)G * SW);  // [ncores][SW*32] axon at each sorted position
+    int8_t *wt = reinterpret_cast<int8_t *>(perm + (size_t)G * SW * 32);  // [ncores][SW] type of each sorted word
+    uint32_t *inb = reinterpret_cast<uint32_t *>(wt + (((size_t)G * SW + 15) & ~(size_t)15));  // [t_in][in_words] inputs
     const unsigned nblocks = gridDim.x;
     unsigned gen = 0;
 
-    const uint32_t xbytes = (uint32_t)ncores * N * AW * 4u;
+    const uint32_t xbytes = (uint32_t)ncores * N * SW * 4u;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(&bar, xbytes);
-        bulk_g2s(xs, a.xbarT + (size_t)c_first * N * AW, xbytes, &bar);
+        bulk_g2s(xs, a.xbarT + (size_t)c_first * N * SW, xbytes, &bar);
     }
-    for (int i = tid; i < ncores * K * AW; i += blockDim.x) tm[i] = a.tmask[(size_t)c_first * K * AW + i];
-    for (int i = tid; i < ncores * a.A; i += blockDim.x) perm[i] = a.axperm[(size_t)c_first * a.A + i];
+    for (int i = tid; i < ncores * SW * 32; i += blockDim.x) perm[i] = a.axperm[(size_t)c_first * SW * 32 + i];
+    for (int i = tid; i < ncores * SW; i += blockDim.x) wt[i] = a.wtype[(size_t)c_first * SW + i];
     int lam = 0, pth = 0, nth = 0, rst = 0, v0 = 0;
     uint32_t wr[4] = {0u, 0u, 0u, 0u};
     uint2 dd = make_uint2(0u, 0u);
@@ -289,7 +270,6 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     }
     if (tid < kMaxWindowCores * 4) red[tid / 4][tid % 4] = 0u;
     __syncthreads();
-    for (int i = tid; i < ncores * AW; i += blockDim.x) wt[i] = word_type(tm + (size_t)(i / AW) * K * AW, AW, K, i % AW);
     const bool ok0 = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok0)) {
         if (tid == 0) atomicExch(a.err, kErrTimeout);
@@ -341,13 +321,12 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                 }
                 __syncthreads();
             }
-            gather_sorted(sb, perm, a.A, AW, ncores, spb, tid, blockDim.x);
+            gather_sorted(sb, perm, AW, SW, ncores, spb, tid, blockDim.x);
             __syncthreads();
             bool fire = false;
             if (has_core) {
                 uint32_t syn = 0u;
-                const int dv = integrate_sorted(spb + cg * AW, xs + (size_t)cg * AW * N + n, N, tm + (size_t)cg * K * AW,
-                                                wt + cg * AW, AW, K, wr, syn);
+                const int dv = integrate_sorted(spb + cg * SW, xs + (size_t)cg * SW * N + n, N, wt + cg * SW, SW, wr, syn);
                 int x = V + dv + lam;
                 fire = x >= pth;
                 if (fire)
@@ -417,8 +396,8 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
 // otherwise, so the caller can use the per-tick launches instead.
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     const int threads = w.G * w.p.N;
-    const size_t smem = ((size_t)w.G * w.p.N * w.p.AW + (size_t)w.G * w.p.K * w.p.AW + 2 * (size_t)w.G * w.p.AW) * 4 +
-                        (size_t)w.G * w.p.A * 2 + (((size_t)w.G * w.p.AW + 15) & ~(size_t)15) +
+    const size_t smem = ((size_t)w.G * w.p.N * w.p.SW + (size_t)w.G * w.p.AW + (size_t)w.G * w.p.SW) * 4 +
+                        (size_t)w.G * w.p.SW * 32 * 2 + (((size_t)w.G * w.p.SW + 15) & ~(size_t)15) +
                         (w.stream ? 0 : (size_t)w.t_in * w.p.in_words) * 4;
     cudaError_t e = raise_smem_limit((const void *)plain_window_kernel, (int)smem);
     if (e != cudaSuccess) return e;
@@ -441,8 +420,8 @@ __global__ void plain_reset_v_kernel(int *V, const int *v0, long long per_sample
         V[i] = v0[i % per_sample];
 }
 
-cudaError_t plain_setup_kernel_attrs(int N, int AW) {
-    const int smem = N * AW * 4;
+cudaError_t plain_setup_kernel_attrs(int N, int SW) {
+    const int smem = N * SW * 4;
     if (smem <= 48 * 1024) return cudaSuccess;
     return raise_smem_limit((const void *)plain_tick_kernel, smem);
 }
