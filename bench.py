@@ -38,17 +38,21 @@ L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one batched tick
 # launch from an ncu capture of a 1024-sample case, scaled by the number of
-# (core, tile) items to the 4096-sample launch; valid only for the kernel source
-# it was taken on (see profiles/batched_tick_kernel_mnist512_1024samples.md).
-PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "548641ffe8834a12", "samples": 1024,
+# (core, tile) items to the 4096-sample launch; valid only for the tick kernel's
+# source it was taken on: the sha256 of ranc_batched.cu up to its helper-kernel
+# section (see profiles/batched_tick_kernel_mnist512_1024samples.md).
+PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "dad04dc78ecba147", "samples": 1024,
                     "bytes_per_launch": 644.9e6}
 
 
-def profiled_traffic(n_samples):
+def kernel_source_sha():
     import hashlib
-    src = os.path.join(ROOT, "paper_2404_16208_gb300", "csrc", "ranc_batched.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if sha != PROFILED_TRAFFIC["kernel_source_sha256_prefix"]:
+    src = open(os.path.join(ROOT, "paper_2404_16208_gb300", "csrc", "ranc_batched.cu")).read()
+    return hashlib.sha256(src[:src.index("// Helper kernels: reset")].encode()).hexdigest()[:16]
+
+
+def profiled_traffic(n_samples):
+    if kernel_source_sha() != PROFILED_TRAFFIC["kernel_source_sha256_prefix"]:
         return None
     return PROFILED_TRAFFIC["bytes_per_launch"] * n_samples / PROFILED_TRAFFIC["samples"]
 

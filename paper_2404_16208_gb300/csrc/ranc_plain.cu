@@ -75,20 +75,16 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
     const int lane = n & 31, warp = n >> 5;
     const uint32_t xbytes = (uint32_t)N * SW * 4u;
 
-    if (n == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(&bar, xbytes);
-        bulk_g2s(xs, a.xbarT + (size_t)c * N * SW, xbytes, &bar);
-    }
     const size_t bc = (size_t)b * a.C + c;
     uint32_t *row = a.ring + (bc * kRows + (a.tick & (kRows - 1))) * AW;
     if (n < AW) {
         s[n] = row[n];
         row[n] = 0u;
     }
-    for (int i = n; i < SW * 32; i += blockDim.x) perm[i] = a.axperm[(size_t)c * SW * 32 + i];
-    if (n < SW) wt[n] = a.wtype[(size_t)c * SW + n];
+    if (n == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
     if (n < 4) red[n] = 0u;
     __syncthreads();
 
@@ -103,7 +99,19 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
             }
         }
     }
-    bool ok = mbar_wait_bounded(&bar, 0);
+    // A core with no active axon this tick needs neither its crossbar nor its
+    // weights (dV = 0): with many idle cores the tick is bound by these loads.
+    __syncthreads();  // the input bits are in s
+    const bool active = __syncthreads_or(n < AW && s[n] != 0u);
+    if (active && n == 0) {
+        mbar_arrive_expect_tx(&bar, xbytes);
+        bulk_g2s(xs, a.xbarT + (size_t)c * N * SW, xbytes, &bar);
+    }
+    if (active) {
+        for (int i = n; i < SW * 32; i += blockDim.x) perm[i] = a.axperm[(size_t)c * SW * 32 + i];
+        if (n < SW) wt[n] = a.wtype[(size_t)c * SW + n];
+    }
+    bool ok = !active || mbar_wait_bounded(&bar, 0);
     if (a.stall_test && blockIdx.x == 0 && blockIdx.y == 0) {
         // Failure-detection test: a barrier that never completes; the bounded
         // wait must give up and report, not hang.
@@ -117,19 +125,22 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
     }
     if (__syncthreads_or(!ok)) {
         if (n == 0) atomicExch(a.err, kErrTimeout);
-        mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
+        if (active) mbar_wait_bounded(&bar, 0);  // let the copy land before the CTA exits
         return;
     }
 
     // Crossbar integration over the type-sorted active axons (word w of
     // neuron n's row at xs[w * N + n]: a warp reads consecutive words, free of
     // bank conflicts); the per-type counts sum to the synaptic events.
-    gather_sorted(s, perm, AW, SW, 1, sp, n, blockDim.x);
-    __syncthreads();
-    const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
-    const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
     uint32_t syn = 0u;
-    const int dv = integrate_sorted(sp, xs + n, N, wt, SW, wr, syn);
+    int dv = 0;
+    if (active) {
+        gather_sorted(s, perm, AW, SW, 1, sp, n, blockDim.x);
+        __syncthreads();
+        const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
+        const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
+        dv = integrate_sorted(sp, xs + n, N, wt, SW, wr, syn);
+    }
 
     // Leak, thresholds, reset.
     const int4 pr = a.prm[(size_t)c * N + n];  // leak, pos_thr, neg_thr, reset
