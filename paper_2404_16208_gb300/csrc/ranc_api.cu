@@ -803,6 +803,9 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
         sim->ticks_total += sim->win_ticks;
         sim->tick = sim->win_tick_after;
         sim->v_lazy = 0;
+        sim->sclock = sim->win_sclock_after;  // the recorded ticks stamp with the recorded clock
+        sim->all_active_ticks = 0;
+        sim->pend_dirty = sim->win_pend_after;
         CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
         ++sim->graph_replays;
         return RANC_OK;
@@ -841,6 +844,8 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
     sim->win_launches = sim->launches - l0;
     sim->win_ticks = sim->ticks_total - t0;
     sim->win_tick_after = sim->tick;
+    sim->win_sclock_after = sim->sclock;
+    sim->win_pend_after = sim->pend_dirty;
     ++sim->graph_captures;
     CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
     return RANC_OK;

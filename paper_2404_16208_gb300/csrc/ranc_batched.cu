@@ -56,8 +56,15 @@ namespace {
 
 constexpr int kWorkers = 16;                 // warps 0-15: operand build + epilogue
 constexpr int kMmaWarp = 16;                 // warp 16: TMEM, TMA, MMA issue
-constexpr int kThreads = (kWorkers + 1) * 32;
+constexpr int kThreads = (kWorkers + 4) * 32;  // warps 16-19: one warpgroup, warp 16 issues the MMAs
+// Registers per thread after the prologue: the issuer's warpgroup gives up
+// registers that the workers take (setmaxnreg).  The launch provides
+// kThreads * 96 = 61440; 16 * 32 * kRegWorker + 4 * 32 * kRegIssuer = 59392
+// (per SM sub-partition: 4 worker warps and 1 issuer-group warp, 14848 of 16384).
+constexpr int kRegWorker = 104, kRegIssuer = 48;
+static_assert(kWorkers * 32 * kRegWorker + 4 * 32 * kRegIssuer <= kThreads * 96, "register split exceeds the launch");
 constexpr uint32_t kBlockBytes = 128u * 128u;  // one 64-axon K-block: 128 weight rows or 128 samples x 64 fp16
+constexpr int kClsCap = 16384;                 // items of a CTA whose classes are kept in shared memory
 
 struct TickArgs {
     int C, A, N, NH, KB, T, n_valid, Lpad, in_ticks, n_out, neg_mode, items;
@@ -65,7 +72,7 @@ struct TickArgs {
     const int4 *prm;
     const uint2 *dst;
     const int *fin_ptr, *fin_line;
-    const uint16_t *outdeg;
+    const uint32_t *outdeg;  // [C][A] connections of each axon
     const uint4 *inT;
     const int *v0;           // non-NULL: the potentials are still the reset values v0 [C][N] (V is not read)
     void *V;
@@ -77,7 +84,51 @@ struct TickArgs {
     uint32_t *olog;          // NULL, or this tick's output-bus log: sample b < olog_rows, id -> olog[b * olog_stride + id]
     long long olog_stride;
     int olog_rows;
+    // Item activity (see item_class).  Item it = c * T + j.
+    const uint8_t *stamp_row;  // [items] stamps of this tick's scheduler row
+    uint8_t *stamp;            // [16][spitch]: a delivery into row r of item it writes stamp[r][it] = its cycle
+    long long spitch;
+    uint32_t sclock;           // stamp clock of this tick (== tick mod 16); its cycle is (sclock >> 4) mod 256
+    int all_active;            // every row may hold bits (imported state): no item is idle
+    const uint8_t *core_flags; // [C] bit 0: some input line drives the core; bit 1: its idle ticks can be deferred
+    const uint8_t *pend_in;    // [items] idle ticks deferred before this tick
+    uint8_t *pend_out;         // [items] idle ticks deferred after this tick
+    int cost_active, cost_idle, cost_lazy, cost_wake;  // relative costs for the split of the items over the CTAs
 };
+
+constexpr int kPendMax = 250;  // deferred idle ticks of an item are applied before this many accumulate
+
+// Work classes of an item in one tick.
+//   2 active: its scheduler row may hold bits, or input lines drive its core
+//     in this tick: full update (operand build, MMA, epilogue).
+//   1 idle: no synaptic input: no row or input is read, the operand is zero
+//     and only its first K-step is issued (dV = W * 0 = 0), so the item takes
+//     the same epilogue as an active one.
+//   0 lazy: idle, and the core's idle tick is a deferred map (every neuron has
+//     leak <= 0, theta- < theta+, reset < theta+, v0 < theta+, saturating
+//     negative threshold): no potential is stored at or above theta+, so with
+//     dV = 0 nothing fires and V <- max(V + leak, theta-); k such ticks compose
+//     to V <- max(V + k * leak, theta-).  The item only counts the tick; the
+//     count is applied by the next update that reads V (or before a state
+//     read).  Never in the first tick after a reset (V is v0 and unwritten).
+// A row holds bits only after a delivery into it, and every delivery writes
+// the row's stamp with the cycle of the tick that will read it, so an item
+// whose stamp differs has an empty row.  An equal stamp left over from an
+// earlier cycle only makes an empty item "active", which is still exact.
+// The class from the item's stamp, deferred ticks and core flags.
+__device__ __forceinline__ int class_from(const TickArgs &a, uint8_t stamp, uint8_t pend, uint8_t cflags) {
+    if (a.all_active || stamp == (uint8_t)(a.sclock >> 4) || (a.tick < (long long)a.in_ticks && (cflags & 1)))
+        return 2;
+    if (!a.v0 && (cflags & 2) && pend < kPendMax) return 0;
+    return 1;
+}
+__device__ __forceinline__ int item_class(const TickArgs &a, int it) {
+    return class_from(a, a.stamp_row[it], a.pend_in[it], a.core_flags[it / a.T]);
+}
+
+__device__ __forceinline__ int class_cost(const TickArgs &a, int cls) {
+    return cls == 2 ? a.cost_active : cls == 1 ? a.cost_idle : a.cost_lazy;
+}
 
 // ---------------------------------------------------------------------------
 // tcgen05 / TMA wrappers (inline PTX)
@@ -258,6 +309,31 @@ __device__ __forceinline__ uint4 v_splat(int x) {
     return make_uint4(w, w, w, w);
 }
 
+// Deferred idle ticks of a lazy item: x <- max(x + pl, theta-) on every
+// potential of a unit (pl = ticks * leak <= 0; the result lies in
+// [theta-, x], so it is exact in every storage format).
+template <typename VT, int kVecs>
+__device__ __forceinline__ void defer_apply(uint4 (&q)[kVecs], int pl, int nth) {
+#pragma unroll
+    for (int e = 0; e < kVecs; ++e) {
+        uint32_t w[4] = {q[e].x, q[e].y, q[e].z, q[e].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (std::is_same<VT, __half>::value) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+                const __half2 r = __floats2half2_rn(fmaxf(f.x + (float)pl, (float)nth), fmaxf(f.y + (float)pl, (float)nth));
+                w[k] = *reinterpret_cast<const uint32_t *>(&r);
+            } else if constexpr (sizeof(VT) == 2) {
+                const int lo = max((int)(int16_t)(w[k] & 0xFFFFu) + pl, nth), hi = max(((int)w[k] >> 16) + pl, nth);
+                w[k] = ((uint32_t)lo & 0xFFFFu) | ((uint32_t)hi << 16);
+            } else {
+                w[k] = (uint32_t)max((int)w[k] + pl, nth);
+            }
+        }
+        q[e] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // Element offset of potential (tile j, core c, neuron n, sample 32*cc + i) in
 // the interleaved layout described at the top of this file.
 template <typename VT>
@@ -270,23 +346,160 @@ __device__ __forceinline__ size_t v_index(int j, int c, int cc, int n, int i, in
 // The tick kernel
 // ---------------------------------------------------------------------------
 
+// Output-bus events of one warp's 32-sample unit: one warp-wide pass per
+// output neuron that fired (olanes: the lanes holding one); lane i adds sample
+// bs = (first sample of the unit) + i, so no lane loops over spikes.
+__device__ __noinline__ void out_bus(const TickArgs &a, uint32_t olanes, uint32_t live, uint32_t id, int bs) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *const out = a.out, *const olog = a.olog;
+    const int n_out = a.n_out, olog_rows = a.olog_rows;
+    const long long olog_stride = a.olog_stride;
+    while (olanes) {
+        const int L = __ffs(olanes) - 1;
+        olanes &= olanes - 1u;
+        const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
+        const uint32_t idL = __shfl_sync(0xffffffffu, id, L);
+        if ((mL >> lane) & 1u) {
+            atomicAdd(out + (size_t)bs * n_out + idL, 1u);
+            if (olog && bs < olog_rows) atomicAdd(olog + (size_t)bs * olog_stride + idL, 1u);
+        }
+    }
+}
+
+// Split of one tick's items over the CTAs, run by every thread of a CTA at
+// kernel start (kept out of line so that it does not weigh on the register
+// allocation of the item loop).  CTA b takes the items whose cost prefix P
+// (exclusive, in item order) satisfies b * W <= P * G < (b + 1) * W, W the
+// total cost and G the grid; every CTA computes the same sums.  On return
+// cut_sh holds this CTA's range [i0, i1); when the range fits kClsCap, cls_sm
+// holds the class of each of its items (bit 2: deferred idle ticks before
+// this tick); pend_out holds the deferred ticks after this tick of each of its
+// items; flags_sh bit 0 is set when some item applies deferred ticks in this
+// tick, bit 1 when some item starts deferring (its spike masks are cleared).
+__device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, int *cut_sh, uint8_t *cls_sm,
+                                         int *flags_sh) {
+    // The arguments this function reads, once (a reference to the kernel's
+    // argument block is a generic pointer here: every field read would be a load).
+    const uint8_t *const stamp_row = a.stamp_row, *const pend_in = a.pend_in, *const core_flags = a.core_flags;
+    uint8_t *const pend_out = a.pend_out;
+    const int items = a.items, T = a.T;
+    const bool all_active = a.all_active != 0, first = a.v0 != nullptr, inputs = a.tick < (long long)a.in_ticks;
+    const uint8_t cycle = (uint8_t)(a.sclock >> 4);
+    const int c_act = a.cost_active, c_idle = a.cost_idle, c_lazy = a.cost_lazy, c_wake = a.cost_wake;
+    // As class_from, on those copies.
+    auto cls_from = [&](uint8_t stamp, uint8_t pend, uint8_t cflags) -> int {
+        if (all_active || stamp == cycle || (inputs && (cflags & 1))) return 2;
+        if (!first && (cflags & 2) && pend < kPendMax) return 0;
+        return 1;
+    };
+    // Thread tid classifies items [tid * per, tid * per + per), a multiple of
+    // 16, reading stamps and deferred counts as 16-byte vectors (rows are
+    // padded to 128 bytes).
+    const int per = ((items + kThreads - 1) / kThreads + 15) & ~15;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t0 = min(items, tid * per), t1 = min(items, t0 + per);
+    // fn(it, class, deferred idle ticks) for the items [u0, u1) of this thread.
+    auto visit = [&](int u0, int u1, auto &&fn) {
+        if (u0 >= u1) return;
+        int c = u0 / T, j = u0 - c * T;
+        uint8_t cf = core_flags[c];
+        for (int b16 = u0 & ~15; b16 < u1; b16 += 16) {
+            const uint4 sv = *reinterpret_cast<const uint4 *>(stamp_row + b16);
+            const uint4 pv = *reinterpret_cast<const uint4 *>(pend_in + b16);
+            const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w}, pw[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int it = b16 + k;
+                if (it < u0) continue;
+                if (it >= u1) break;
+                if (j == T) {
+                    j = 0;
+                    cf = core_flags[++c];
+                }
+                ++j;
+                const uint8_t pn = (uint8_t)(pw[k >> 2] >> (8 * (k & 3)));
+                fn(it, cls_from((uint8_t)(sw[k >> 2] >> (8 * (k & 3))), pn, cf), first ? 0 : (int)pn);
+            }
+        }
+    };
+    // Cost of an item: its class, plus the pass that applies deferred ticks
+    // when it wakes up, plus the spike-mask clearing of a first lazy tick.
+    auto cost_of = [&](int cls, int pend) -> int {
+        return (cls == 2 ? c_act : cls == 1 ? c_idle : c_lazy) + (cls != 0 && pend ? c_wake : 0) + (cls == 0 && !pend ? 1 : 0);
+    };
+    long long csum = 0;
+    visit(t0, t1, [&](int, int cls, int pend) { csum += cost_of(cls, pend); });
+    long long cinc = csum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, cinc, o);
+        if (lane >= o) cinc += y;
+    }
+    if (lane == 31) wsum_sh[warp] = cinc;
+    __syncthreads();
+    {
+        long long P = 0, W = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const long long x = wsum_sh[w];
+            if (w < warp) P += x;
+            W += x;
+        }
+        P += cinc - csum;
+        // P * G < b * W  <=>  P < ceil(b * W / G): the first item of CTA b is
+        // the first whose prefix reaches that bound.
+        const long long G = gridDim.x;
+        const long long lo = ((long long)blockIdx.x * W + G - 1) / G, hi = ((long long)(blockIdx.x + 1) * W + G - 1) / G;
+        // Items of this thread whose prefix lies below a bound: all of them,
+        // none, or (for at most one thread per bound) a walk.
+        int n0 = 0, n1 = 0;
+        const long long Pend = P + csum;
+        const bool walk0 = P < lo && Pend > lo, walk1 = P < hi && Pend > hi;
+        if (!walk0) n0 = Pend <= lo ? t1 - t0 : 0;
+        if (!walk1) n1 = Pend <= hi ? t1 - t0 : 0;
+        if (walk0 || walk1)
+            visit(t0, t1, [&](int, int cls, int pend) {
+                if (walk0) n0 += P < lo;
+                if (walk1) n1 += P < hi;
+                P += cost_of(cls, pend);
+            });
+        n0 = __reduce_add_sync(0xffffffffu, n0);
+        n1 = __reduce_add_sync(0xffffffffu, n1);
+        if (lane == 0 && (n0 | n1)) {
+            atomicAdd(&cut_sh[0], n0);
+            atomicAdd(&cut_sh[1], n1);
+        }
+    }
+    __syncthreads();
+    const int i0 = cut_sh[0], i1 = cut_sh[1];
+    const bool cls_cached = i1 - i0 <= kClsCap;
+    int fl = 0;
+    visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend) {
+        if (cls_cached) cls_sm[it - i0] = (uint8_t)(cls | (pend ? 4 : 0));
+        fl |= (pend && cls != 0 ? 1 : 0) | (!pend && cls == 0 ? 2 : 0);
+        pend_out[it] = cls == 0 ? (uint8_t)(pend + 1) : (uint8_t)0;
+    });
+    if (fl) atomicOr(flags_sh, fl);
+}
+
 template <typename VT, int kNegReset>
-__global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArgs a, const __grid_constant__ CUtensorMap wmap) {
+__global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_constant__ TickArgs a, const __grid_constant__ CUtensorMap wmap) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full, s_free, acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
+    __shared__ long long wsum_sh[kThreads / 32];
+    __shared__ int cut_sh[2];
+    __shared__ int flags_sh;  // bit 0: some item applies deferred idle ticks; bit 1: some item starts deferring
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NH = a.NH, KB = a.KB, C = a.C, A = a.A, N = a.N, T = a.T;
     uint8_t *Wsm = base;                                   // [NH][KB] blocks of 128 rows x 128 B
     uint8_t *Ssm = Wsm + (size_t)NH * KB * kBlockBytes;    // [KB] blocks of [8 groups][2 halves][8 axons][64 samples]
     uint2 *lut = reinterpret_cast<uint2 *>(Ssm + (size_t)KB * kBlockBytes);  // 16 x 8 B: one row of banks
+    // Per item of this CTA: class (bits 0-1) and "has deferred idle ticks" (bit 2).
+    uint8_t *cls_sm = reinterpret_cast<uint8_t *>(lut) + 4096;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = (int)((long long)blockIdx.x * a.items / gridDim.x);
-    const int i1 = (int)((long long)(blockIdx.x + 1) * a.items / gridDim.x);
-    const int n_items = i1 - i0;
     const int r0 = (int)(a.tick & (kRows - 1));
 
     // 4 fp16 values (1.0 or 0.0) for every nibble of spike bits.  The table is
@@ -311,11 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         abort_sh = 0;
         fence_mbar_init();
     }
+    if (tid < 2) cut_sh[tid] = 0;
+    if (tid == 0) flags_sh = 0;
     if (warp == kMmaWarp) tmem_alloc(&tmem_base_sh, a.tmem_cols);
+    split_items(a, wsum_sh, cut_sh, cls_sm, &flags_sh);
+    const int i0 = cut_sh[0], i1 = cut_sh[1];
+    const int n_items = i1 - i0;
+    const bool cls_cached = n_items <= kClsCap;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    auto cls_of = [&](int it) -> int { return cls_cached ? cls_sm[it - i0] & 3 : item_class(a, it); };
+    // Idle ticks deferred by item it before this tick (0 in the first tick after a reset).
+    auto deferred_of = [&](int it) -> int {
+        if (a.v0 || (cls_cached && !(cls_sm[it - i0] & 4))) return 0;
+        return a.pend_in[it];
+    };
 
     auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
         if (abort_sh) return false;
@@ -326,6 +551,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
     };
 
     if (warp < kWorkers) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kRegWorker) : "memory");
         // ------------------------------------------------------------ workers
         // Iteration li: (1) build the operand tile S of item li (the tensor
         // core is idle, waiting for it); (2) epilogue of item li-1 while the
@@ -342,10 +568,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
         const int n = h * 128 + q * 32 + lane;
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;  // 16-byte vectors per 32 potentials
         constexpr bool kHalf = std::is_same<VT, __half>::value;
-        // Units whose potentials are loaded before the build: both for int16
-        // (registers allow it); one for int32 and fp16 (the fp16 update keeps
-        // more values live, and a second early unit would spill).
-        constexpr int kPre = (sizeof(VT) == 2 && !kHalf) ? 2 : 1;
+        // Units whose potentials are loaded before the build: one (a second
+        // early unit would spill registers in every storage format).
+        constexpr int kPre = 1;
         VT *Vg = reinterpret_cast<VT *>(a.V);
         // Build task of this lane: axon rax, samples 64*rhf .. 64*rhf+63 (two
         // scheduler words, read as one 8-byte vector: a warp reads 256
@@ -391,10 +616,54 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
             }
             return w;
         };
-        uint2 wnext = n_items > 0 ? load_words(i0) : make_uint2(0u, 0u);
+        // Class of item li of this CTA (0 past the end).
+        auto cls_at = [&](int li) -> int { return li >= 0 && li < n_items ? cls_of(i0 + li) : 0; };
+        // Items that are updated in this tick after deferring idle ticks: the
+        // deferred ticks are applied first, each thread to the potentials that
+        // its own epilogue reads later (program order, no barrier needed).
+        if (flags_sh & 1)
+            for (int li = 0; li < n_items; ++li) {
+                const int it = i0 + li, pe = cls_at(li) != 0 ? deferred_of(it) : 0;
+                if (!pe) continue;
+                const int c = it / T, j = it % T;
+                const int4 pr = a.prm[(size_t)c * N + n];
+                for (int k = 0; k < nu; ++k) {
+                    uint4 *vp = reinterpret_cast<uint4 *>(Vg + v_index<VT>(j, c, cc0 + k, n & ~31, 0, C, N)) + lane;
+                    uint4 q[kVecs];
+#pragma unroll
+                    for (int e = 0; e < kVecs; ++e) q[e] = vp[e * 32];
+                    defer_apply<VT>(q, pe * pr.x, pr.z);
+#pragma unroll
+                    for (int e = 0; e < kVecs; ++e) vp[e * 32] = q[e];
+                }
+            }
+        // Items that start deferring in this tick: their spike masks are zero
+        // (and stay so while they keep deferring).
+        if (flags_sh & 2)
+            for (int li = 0; li < n_items; ++li)
+                if (cls_at(li) == 0 && deferred_of(i0 + li) == 0) {
+                    const int it = i0 + li, c = it / T, j = it % T;
+                    for (int k = 0; k < nu; ++k) a.spk[(((size_t)j * C + c) * 4 + cc0 + k) * N + n] = 0u;
+                }
+        // Iteration li builds the operand of item li and runs the epilogue of
+        // item li - 1; lazy items take neither (their tick is recorded by the
+        // split), and an idle item's operand is zero (its row and inputs are
+        // known to be empty).  The row words of the next active item are
+        // loaded one build ahead.
+        auto next_nl = [&](int li) -> int {
+            while (li < n_items && cls_at(li) == 0) ++li;
+            return li;
+        };
+        uint2 wnext = make_uint2(0u, 0u);
+        {
+            const int l0 = next_nl(0);
+            if (l0 < n_items && cls_at(l0) == 2) wnext = load_words(i0 + l0);
+        }
+        int nb = 0;  // items whose operand this warp has built (operand and accumulator phases)
         for (int li = 0; li <= n_items; ++li) {
+            if (cls_at(li) == 0 && cls_at(li - 1) == 0) continue;  // nothing to build, no epilogue
             // Potentials of the epilogue item (li - 1), loaded before the build.
-            const int le = li - 1, ite = i0 + le;
+            const int le = cls_at(li - 1) != 0 ? li - 1 : -1, ite = i0 + le;
             const int ce = ite / T, je = ite % T;
             uint4 vb[kPre][kVecs];
             auto vaddr = [&](int k) {  // this lane's first 16-byte vector of unit k
@@ -418,19 +687,23 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 }
             }
             // ---- (1) build S of item li
-            if (li < n_items) {
+            if (cls_at(li) != 0) {
                 const int it = i0 + li, c = it / T, j = it % T;
-                if (!wait(&s_free, (li & 1) ^ 1)) break;
+                const bool act = cls_at(li) == 2;
+                if (!wait(&s_free, (nb & 1) ^ 1)) break;
                 if (c != bc) {
                     if (has_task) odr = a.outdeg[(size_t)c * A + rax];
                     bc = c;
                 }
                 const uint2 wcur = wnext;
-                if (li + 1 < n_items) wnext = load_words(it + 1);
+                {
+                    const int ln = next_nl(li + 1);
+                    wnext = ln < n_items && cls_at(ln) == 2 ? load_words(i0 + ln) : make_uint2(0u, 0u);
+                }
                 unsigned long long ev = 0;
                 if (has_task) {
                     uint2 *row = reinterpret_cast<uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
-                    row[rax * 2 + rhf] = make_uint2(0u, 0u);
+                    if (act) row[rax * 2 + rhf] = make_uint2(0u, 0u);
                     const int m0 = j * 128 + rhf * 64;
                     ev = (unsigned long long)odr * (unsigned)(__popc(wcur.x & valid_mask(a.n_valid, m0)) +
                                                                __popc(wcur.y & valid_mask(a.n_valid, m0 + 32)));
@@ -452,13 +725,16 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_full);
+                ++nb;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
                 if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
             }
             // ---- (2) epilogue of item li - 1
             if (le >= 0) {
-                const int buf = le & 1;
+                // Items with an MMA before this one: nb counts those up to item li.
+                const int ne = nb - (cls_at(li) != 0 ? 1 : 0) - 1;
+                const int buf = ne & 1;
                 if (ce != pc) {
                     const int4 pr = a.prm[(size_t)ce * N + n];  // leak, pos_thr, neg_thr, reset
                     lam = pr.x - 0x4B400000;  // folds the bias of f32_bits_minus_bias
@@ -475,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                     dd = a.dst[(size_t)ce * N + n];
                     pc = ce;
                 }
-                if (!wait(&acc_full[buf], (le >> 1) & 1)) break;
+                if (!wait(&acc_full[buf], (ne >> 1) & 1)) break;
                 tc_fence_after();
                 const uint32_t kind = dest_kind(dd);
                 uint32_t n_sp = 0, n_pk = 0, n_out = 0;
@@ -564,6 +840,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                         atomicOr(reinterpret_cast<uint32_t *>(a.ring) + ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
                                  mask);
                         n_pk += __popc(live);
+                        // The destination row's stamp: the cycle of the tick that reads it.
+                        a.stamp[(size_t)r * a.spitch + (size_t)dd.x * T + je] = (uint8_t)((a.sclock + dest_delay(dd)) >> 4);
                     }
                     // Output bus: one warp-wide pass per output neuron that fired;
                     // lane i adds sample cc*32 + i, so no lane loops over spikes.
@@ -595,14 +873,25 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 }
             }
         }
-    } else if (lane == 0) {
+    } else {
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kRegIssuer) : "memory");
+      if (warp == kMmaWarp && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         int loaded = -1;
         uint32_t nw = 0, nd = 0;
         bool w_pending = false;
         const size_t vtile = (size_t)4 * N * 32 * sizeof(VT);
-        for (int it = i0; it < i1; ++it) {
-            const int li = it - i0, c = it / T, buf = li & 1;
+        int na = 0;  // items issued
+        // The items that are not lazy, in order (as the workers visit them).
+        auto next_nl = [&](int li) -> int {
+            while (li < n_items && cls_of(i0 + li) == 0) ++li;
+            return li;
+        };
+        int lc = next_nl(0);
+        int l1 = lc < n_items ? next_nl(lc + 1) : n_items;
+        for (; lc < n_items; lc = l1, l1 = l1 < n_items ? next_nl(l1 + 1) : n_items) {
+            const int it = i0 + lc, c = it / T, buf = na & 1;
+            const bool act = cls_of(it) == 2;
             if (c != loaded) {
                 if (loaded >= 0) {  // every MMA reading the old weights has finished
                     mma_commit(&bar_drain);
@@ -619,17 +908,23 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
                 ++nw;
                 loaded = c;
             }
-            if (it + 1 < i1) {
-                const int c1 = (it + 1) / T, j1 = (it + 1) % T;
+            if (l1 < n_items) {  // potentials of the next item
+                const int c1 = (i0 + l1) / T, j1 = (i0 + l1) % T;
                 prefetch_l2(reinterpret_cast<const uint8_t *>(a.V) + ((size_t)j1 * C + c1) * vtile, (uint32_t)vtile);
+                const int l2 = next_nl(l1 + 1);
+                if (l2 < n_items && cls_of(i0 + l2) == 2) {  // scheduler row of the one after
+                    const int c2 = (i0 + l2) / T, j2 = (i0 + l2) % T;
+                    prefetch_l2(a.ring + (((size_t)j2 * C + c2) * kRows + r0) * A, (uint32_t)A * 16u);
+                }
             }
-            if (it + 2 < i1) {
-                const int c2 = (it + 2) / T, j2 = (it + 2) % T;
-                prefetch_l2(a.ring + (((size_t)j2 * C + c2) * kRows + r0) * A, (uint32_t)A * 16u);
-            }
-            if (!wait(&acc_empty[buf], ((li >> 1) & 1) ^ 1)) break;
-            if (!wait(&s_full, li & 1)) break;
+            if (!wait(&acc_empty[buf], ((na >> 1) & 1) ^ 1)) break;
+            if (!wait(&s_full, na & 1)) break;
             tc_fence_after();
+            if (!act) {  // idle: the zero operand's first K-step gives dV = 0
+                for (int hh = 0; hh < NH; ++hh)
+                    mma_f16(tmem + (uint32_t)(buf * NH * 128 + hh * 128), smem_desc_kmajor(smem_u32(Wsm + (size_t)hh * KB * kBlockBytes)),
+                            smem_desc_mn(smem_u32(Ssm)), false);
+            } else
             for (int kb = 0; kb < KB; ++kb) {
 #pragma unroll 1
                 for (int hh = 0; hh < NH; ++hh) {
@@ -643,11 +938,13 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const TickArg
             }
             mma_commit(&s_free);
             mma_commit(&acc_full[buf]);
+            ++na;
         }
         // Drain: all MMAs issued by this thread complete before tensor memory is freed.
         mma_commit(&bar_drain);
         mbar_wait_bounded(&bar_drain, nd & 1);
         if (w_pending) mbar_wait_bounded(&bar_w, nw & 1);  // a weight load still in flight
+      }
     }
     tc_fence_before();
     __syncthreads();
@@ -675,6 +972,29 @@ __global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long ve
         if constexpr (sizeof(VT) == 2) w = (uint32_t)(*reinterpret_cast<const uint16_t *>(&x)) * 0x10001u;
         else w = (uint32_t)x;
         p[e] = make_uint4(w, w, w, w);
+    }
+}
+
+// Applies the idle ticks that lazy items deferred: V <- max(V + k * leak,
+// theta-) for k = pend[c * T + j] (exact: the result lies in [theta-, V]).
+// Vector e of the interleaved layout as in batched_reset_v.
+template <typename VT>
+__global__ void batched_catch_up(VT *V, const uint8_t *pend, const int4 *prm, int C, int N, int T, long long vecs) {
+    constexpr int P = 32 * (int)sizeof(VT) / 16, E = 16 / (int)sizeof(VT);
+    uint4 *p = reinterpret_cast<uint4 *>(V);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vecs; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / (32 * P);  // ((j*C + c)*4 + cc)*(N/32) + n/32
+        const int n = (int)(g % (N / 32)) * 32 + (int)(e % 32);
+        const long long jc = g / (N / 32) / 4;
+        const int c = (int)(jc % C), j = (int)(jc / C);
+        const int k = pend[(size_t)c * T + j];
+        if (k == 0) continue;
+        const int4 pr = prm[(size_t)c * N + n];
+        uint4 u = p[e];
+        VT *x = reinterpret_cast<VT *>(&u);
+#pragma unroll
+        for (int i = 0; i < E; ++i) x[i] = v_from_int<VT>(max(v_to_int<VT>(x[i]) + k * pr.x, pr.z));
+        p[e] = u;
     }
 }
 
@@ -773,9 +1093,17 @@ struct Batched {
     size_t smem = 0;
     __half *wfold = nullptr;
     int *fin_ptr = nullptr, *fin_line = nullptr;
-    uint16_t *outdeg = nullptr;
+    uint32_t *outdeg = nullptr;
     uint4 *inT = nullptr;
     size_t inT_cap = 0;
+    // Item activity: delivery stamps [16][spitch], deferred idle ticks
+    // [2][spitch] (double-buffered by tick parity), per-core flags.
+    uint8_t *stamp = nullptr, *pend = nullptr, *core_flags = nullptr;
+    long long spitch = 0;
+    bool any_lazy = false;
+    // Relative cost of an active, idle and lazy item and of applying deferred
+    // ticks (the split of a tick's items over the CTAs balances their sum).
+    int cost_active = 16, cost_idle = 16, cost_lazy = 1, cost_wake = 10;
     CUtensorMap wmap;  // 64-byte aligned by its declaration
 };
 
@@ -816,7 +1144,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     bs->Lpad = sim->in_words * 32;
     bs->n_sm = prop.multiProcessorCount;
     bs->tmem_cols = bs->NH == 2 ? 512u : 256u;
-    bs->smem = (size_t)(bs->NH + 1) * bs->KB * kBlockBytes + 256 * 16 + 1024;
+    bs->smem = (size_t)(bs->NH + 1) * bs->KB * kBlockBytes + 256 * 16 + kClsCap + 1024;
     sim->T = (sim->B + kTileS - 1) / kTileS;
     sim->B_pad = sim->T * kTileS;
 
@@ -846,7 +1174,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
 
     // Folded weights W[c][n][a] = connected(a, n) ? w[type(a)][n] : 0 (fp16, exact).
     std::vector<__half> wf((size_t)C * N * A);
-    std::vector<uint16_t> od((size_t)C * A, 0);
+    std::vector<uint32_t> od((size_t)C * A, 0);
     const int NWd = N / 32;
     for (int c = 0; c < C; c++)
         for (int ax = 0; ax < A; ax++) {
@@ -876,23 +1204,43 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         }
         if (fline.empty()) fline.push_back(0);
     }
+    // Per core: driven by an input line; idle ticks deferrable (item_class).
+    std::vector<uint8_t> cfl(C, 0);
+    for (int c = 0; c < C; c++) {
+        const bool driven = fptr[(size_t)c * (A + 1) + A] > fptr[(size_t)c * (A + 1)];
+        bool ok = d->neg_mode == 0;
+        for (int n = 0; n < N && ok; n++) {
+            const size_t i = (size_t)c * N + n;
+            const long long pt = d->pos_thr[i];
+            ok = d->leak[i] <= 0 && d->neg_thr[i] < pt && d->reset[i] < pt && d->v0[i] < pt;
+        }
+        cfl[c] = (uint8_t)((driven ? 1 : 0) | (ok ? 2 : 0));
+        bs->any_lazy = bs->any_lazy || ok;
+    }
+    bs->spitch = ((long long)sim->T * C + 127) / 128 * 128;
     const size_t vsz = sim->vmode == kVInt32 ? 4 : 2;
-    if (dev_alloc((void **)&bs->wfold, wf.size() * 2) != cudaSuccess || dev_alloc((void **)&bs->outdeg, od.size() * 2) != cudaSuccess ||
+    if (dev_alloc((void **)&bs->wfold, wf.size() * 2) != cudaSuccess || dev_alloc((void **)&bs->outdeg, od.size() * 4) != cudaSuccess ||
         dev_alloc((void **)&bs->fin_ptr, fptr.size() * 4) != cudaSuccess ||
         dev_alloc((void **)&bs->fin_line, fline.size() * 4) != cudaSuccess ||
         dev_alloc((void **)&sim->V, (size_t)sim->T * C * 4 * N * 32 * vsz) != cudaSuccess ||
         dev_alloc((void **)&sim->ring, (size_t)sim->T * C * kRows * A * 16) != cudaSuccess ||
         dev_alloc((void **)&sim->spk, (size_t)sim->T * C * 4 * N * 4) != cudaSuccess ||
         dev_alloc((void **)&sim->out, (size_t)sim->B_pad * sim->n_outputs * 4) != cudaSuccess ||
-        dev_alloc((void **)&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess) {
+        dev_alloc((void **)&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess ||
+        dev_alloc((void **)&bs->stamp, (size_t)kRows * bs->spitch) != cudaSuccess ||
+        dev_alloc((void **)&bs->pend, (size_t)2 * bs->spitch) != cudaSuccess ||
+        dev_alloc((void **)&bs->core_flags, (size_t)C) != cudaSuccess) {
         why = "device allocation of the batched state failed";
         return cudaErrorMemoryAllocation;
     }
     sim->cnt_len = (size_t)sim->T * C * 4;
     if ((e = cudaMemcpy(bs->wfold, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->outdeg, od.data(), od.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->fin_ptr, fptr.data(), fptr.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess) {
+        (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(bs->core_flags, cfl.data(), (size_t)C, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(bs->stamp, 0, (size_t)kRows * bs->spitch)) != cudaSuccess ||
+        (e = cudaMemset(bs->pend, 0, (size_t)2 * bs->spitch)) != cudaSuccess) {
         why = "copy of the batched network arrays";
         return e;
     }
@@ -940,19 +1288,56 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.inT = bs->inT; a.v0 = sim->v_lazy ? sim->v0 : nullptr; a.V = sim->V; a.ring = reinterpret_cast<uint4 *>(sim->ring); a.spk = sim->spk; a.out = sim->out;
     a.cnt = sim->cnt; a.err = sim->err; a.tmem_cols = bs->tmem_cols;
     a.olog = sim->olog_t; a.olog_stride = sim->olog_stride; a.olog_rows = sim->B;
+    // The stamp clock runs with the tick modulo 16 (a reset moves it to the
+    // next multiple of 16).  If the tick was set otherwise (a state import),
+    // the clock jumps ahead and every item counts as active until all rows
+    // written under the old clock have been read.
+    if (((sim->sclock ^ (uint32_t)sim->tick) & (kRows - 1)) != 0) {
+        sim->sclock = ((sim->sclock + 2 * kRows) & ~(uint32_t)(kRows - 1)) | ((uint32_t)sim->tick & (kRows - 1));
+        sim->all_active_ticks = kRows;
+    }
+    a.stamp = bs->stamp; a.spitch = bs->spitch; a.stamp_row = bs->stamp + (size_t)(sim->tick & (kRows - 1)) * bs->spitch;
+    a.sclock = sim->sclock; a.all_active = sim->all_active_ticks > 0;
+    a.core_flags = bs->core_flags;
+    a.pend_in = bs->pend + (size_t)(sim->tick & 1) * bs->spitch;
+    a.pend_out = bs->pend + (size_t)((sim->tick + 1) & 1) * bs->spitch;
+    a.cost_active = bs->cost_active; a.cost_idle = bs->cost_idle; a.cost_lazy = bs->cost_lazy; a.cost_wake = bs->cost_wake;
     const int grid = std::min(bs->n_sm, a.items);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
                                         : (sim->neg_mode ? batched_tick_kernel<int, 1> : batched_tick_kernel<int, 0>);
     kern<<<grid, kThreads, bs->smem, sim->stream>>>(a, bs->wmap);
     sim->v_lazy = 0;  // this tick wrote V and the spike masks
+    sim->sclock++;
+    if (sim->all_active_ticks > 0) --sim->all_active_ticks;
+    if (bs->any_lazy) sim->pend_dirty = 1;
     return cudaGetLastError();
 }
 
 // V <- v0 and no spikes: materialised only when something reads the state
 // before the first tick after a reset (that tick reads v0 itself).
 static cudaError_t batched_materialize(ranc_sim *sim) {
-    if (!sim->v_lazy) return cudaSuccess;
+    Batched *bs = B_of(sim);
+    uint8_t *pend_cur = bs->pend + (size_t)(sim->tick & 1) * bs->spitch;  // what the next tick reads
+    if (!sim->v_lazy) {
+        if (!sim->pend_dirty) return cudaSuccess;
+        const long long vecs = (long long)sim->T * sim->C * 4 * sim->N * (sim->vmode == kVInt32 ? 8 : 4);
+        const unsigned g = (unsigned)grid_for(vecs);
+        if (sim->vmode == kVHalf)
+            batched_catch_up<__half><<<g, 256, 0, sim->stream>>>((__half *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+        else if (sim->vmode == kVInt16)
+            batched_catch_up<int16_t><<<g, 256, 0, sim->stream>>>((int16_t *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+        else
+            batched_catch_up<int><<<g, 256, 0, sim->stream>>>((int *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+        sim->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(pend_cur, 0, (size_t)bs->spitch, sim->stream)) != cudaSuccess) return e;
+        sim->pend_dirty = 0;
+        return cudaSuccess;
+    }
+    if (cudaError_t e = cudaMemsetAsync(pend_cur, 0, (size_t)bs->spitch, sim->stream); e != cudaSuccess) return e;
+    sim->pend_dirty = 0;
     const long long total = (long long)sim->T * sim->C * 4 * sim->N * (sim->vmode == kVInt32 ? 8 : 4);  // 16-byte vectors
     if (sim->vmode == kVHalf)
         batched_reset_v<__half><<<(unsigned)grid_for(total), 256, 0, sim->stream>>>((__half *)sim->V, sim->v0, sim->C, sim->N, total);
@@ -970,8 +1355,14 @@ static cudaError_t batched_materialize(ranc_sim *sim) {
 
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
     // Potentials and spike masks: the first tick reads v0 instead of V and
-    // writes every spike mask, so nothing is written here.
+    // writes every spike mask, so nothing is written here (it also ignores
+    // and rewrites the deferred idle ticks).
     sim->v_lazy = 1;
+    sim->pend_dirty = 0;
+    // The tick restarts at 0: the stamp clock moves to the next multiple of 16
+    // past its current cycle, and no row holds bits after the clearing below.
+    sim->sclock = (sim->sclock + 2 * kRows - 1) & ~(uint32_t)(kRows - 1);
+    sim->all_active_ticks = 0;
     // Scheduler rows.  After normal stepping up to tick t, a row can hold
     // bits only if a delivery of tick t' < t targets a tick >= t, i.e. rows
     // t .. t + max_delay - 1 (mod 16): every other row was cleared when it was
@@ -1045,6 +1436,10 @@ cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v, uint32_
 cudaError_t launch_batched_import(ranc_sim *sim, const int *v, const uint32_t *spk, const uint32_t *ring) {
     sim->v_lazy = 0;          // V and the spike masks are overwritten
     sim->ring_all_dirty = 1;  // any row may hold deliveries now
+    sim->all_active_ticks = kRows;  // ... so every item is active until each row has been read once
+    sim->pend_dirty = 0;
+    if (cudaError_t e = cudaMemsetAsync(B_of(sim)->pend, 0, (size_t)2 * B_of(sim)->spitch, sim->stream); e != cudaSuccess)
+        return e;
     const long long total = (long long)sim->B * sim->C * sim->N + (long long)sim->T * sim->C * 4 * sim->N +
                             (long long)sim->T * sim->C * kRows * sim->A * 4;
     if (sim->vmode == kVHalf)
@@ -1114,7 +1509,7 @@ cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, u
 void batched_teardown(ranc_sim *sim) {
     Batched *bs = B_of(sim);
     if (!bs) return;
-    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT};
+    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT, bs->stamp, bs->pend, bs->core_flags};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete bs;

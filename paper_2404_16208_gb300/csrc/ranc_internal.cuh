@@ -103,6 +103,9 @@ struct ranc_sim {
     int v_lazy = 0;                     // batched: V and spike masks are the reset values, not yet written
     int ring_all_dirty = 1;             // batched: any scheduler row may hold bits (full clear on reset)
     int max_delay = 15;                 // batched: largest core-to-core delay of the network
+    uint32_t sclock = 2048;             // batched: stamp clock of the next tick (== tick mod 16)
+    int all_active_ticks = 0;           // batched: ticks left in which every item counts as active
+    int pend_dirty = 0;                 // batched: some item may hold deferred idle ticks
     cudaStream_t stream = nullptr;
     int device = 0;
 
@@ -168,6 +171,8 @@ struct ranc_sim {
     long long win_launches = 0;          // kernels in the recorded sequence
     unsigned long long win_ticks = 0;    // sample ticks it advances
     long long win_tick_after = 0;        // tick counter after it
+    uint32_t win_sclock_after = 0;       // batched stamp clock after it
+    int win_pend_after = 0;              // batched: deferred idle ticks may be held after it
     long long graph_captures = 0, graph_replays = 0;
 
     int sticky = 0;

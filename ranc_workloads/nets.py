@@ -315,3 +315,46 @@ def random_net(seed, grid_w, grid_h, axons=32, neurons=32, n_types=4, density=0.
     return make_net(f"random-{seed}", grid_w, grid_h, cells, syn, atype, w, lk, pt, nt, rs, dest,
                     n_inputs, n_outputs, sorted(fan), v0=vv, weight_bits=weight_bits,
                     neg_mode=neg_mode, meta=dict(seed=seed))
+
+
+def layered_net(seed, layers=(2, 2, 2), axons=128, neurons=256, n_types=4, density=0.3, w_lim=60,
+                weight_bits=12, n_inputs=64, n_outputs=8, fanout_per_line=3, delay_max=6, p_fwd=0.5,
+                p_out=0.1, pthr=(1, 150), nthr=(-150, -1), leak=(-3, 0), reset=(-3, 0), v0=(-3, 0),
+                neg_mode=NEG_SATURATE):
+    """A feed-forward random net on one row of cores: a fraction ``p_fwd`` of
+    the neurons of layer k send to a random core, axon and delay of layer
+    k + 1, a fraction ``p_out`` of the last layer's neurons drive random
+    output-bus ids, and the input lines drive layer 0 only.  Once the inputs
+    stop, activity drains layer by layer, so cores fall idle and wake up again
+    when the inputs resume."""
+    C, A, N, K = int(sum(layers)), axons, neurons, n_types
+    start = np.concatenate([[0], np.cumsum(layers)]).astype(int)
+    cells = [(x, 0) for x in range(C)]
+    syn = rng.bernoulli(seed, S_XBAR, (C, A, N), density)
+    atype = rng.uniform_int(seed, S_TYPE, (C, A), 0, K - 1)
+    w = rng.uniform_int(seed, S_WEIGHT, (C, K, N), -w_lim, w_lim)
+    lk = rng.uniform_int(seed, S_LEAK, (C, N), *leak)
+    pt = rng.uniform_int(seed, S_POSTHR, (C, N), *pthr)
+    nt = rng.uniform_int(seed, S_NEGTHR, (C, N), *nthr)
+    rs = rng.uniform_int(seed, S_RESET, (C, N), *reset)
+    vv = rng.uniform_int(seed, S_RESET, (C, N), v0[0], v0[1], offset=C * N)
+    u = rng.uniform_int(seed, S_DEST, (C, N, 4), 0, 2**31 - 1)
+    dest = empty_dest(C, N)
+    for k in range(len(layers)):
+        for c in range(start[k], start[k + 1]):
+            for n in range(N):
+                r = u[c, n, 0] % 1000
+                if k + 1 < len(layers):
+                    if r < p_fwd * 1000:
+                        dc = start[k + 1] + int(u[c, n, 1] % layers[k + 1])
+                        dest[c, n] = (dc - c, 0, u[c, n, 2] % A, 1 + u[c, n, 3] % delay_max, KIND_CORE)
+                elif r < p_out * 1000:
+                    dest[c, n] = (0, 0, u[c, n, 2] % n_outputs, 1, KIND_OUTPUT)
+    fu = rng.uniform_int(seed, S_DEST, (n_inputs, fanout_per_line, 2), 0, 2**31 - 1, offset=C * N * 4)
+    fan = set()
+    for i in range(n_inputs):
+        for j in range(fanout_per_line):
+            fan.add((i, int(fu[i, j, 0] % layers[0]), int(fu[i, j, 1] % A)))
+    return make_net(f"layered-{seed}", C, 1, cells, syn, atype, w, lk, pt, nt, rs, dest, n_inputs, n_outputs,
+                    sorted(fan), v0=vv, weight_bits=weight_bits, neg_mode=neg_mode,
+                    meta=dict(seed=seed, layers=tuple(layers)))
