@@ -375,9 +375,11 @@ __device__ __noinline__ void out_bus(const TickArgs &a, uint32_t olanes, uint32_
 // holds the class of each of its items (bit 2: deferred idle ticks before
 // this tick); pend_out holds the deferred ticks after this tick of each of its
 // items; flags_sh bit 0 is set when some item applies deferred ticks in this
-// tick, bit 1 when some item starts deferring (its spike masks are cleared).
+// tick, bit 1 when some item starts deferring (its spike masks are cleared);
+// nl_bits has bit k set when item i0 + k is not lazy.  A range that does not
+// fit kClsCap defers nothing: its lazy items are updated as idle ones.
 __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, int *cut_sh, uint8_t *cls_sm,
-                                         int *flags_sh) {
+                                         int *flags_sh, uint32_t *nl_bits) {
     // The arguments this function reads, once (a reference to the kernel's
     // argument block is a generic pointer here: every field read would be a load).
     const uint8_t *const stamp_row = a.stamp_row, *const pend_in = a.pend_in, *const core_flags = a.core_flags;
@@ -398,15 +400,20 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const int per = ((items + kThreads - 1) / kThreads + 15) & ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t0 = min(items, tid * per), t1 = min(items, t0 + per);
+    for (int w = tid; w < kClsCap / 32; w += kThreads) nl_bits[w] = 0u;
     // fn(it, class, deferred idle ticks) for the items [u0, u1) of this thread.
     auto visit = [&](int u0, int u1, auto &&fn) {
         if (u0 >= u1) return;
         int c = u0 / T, j = u0 - c * T;
         uint8_t cf = core_flags[c];
+        uint4 sv = *reinterpret_cast<const uint4 *>(stamp_row + (u0 & ~15));
+        uint4 pv = *reinterpret_cast<const uint4 *>(pend_in + (u0 & ~15));
         for (int b16 = u0 & ~15; b16 < u1; b16 += 16) {
-            const uint4 sv = *reinterpret_cast<const uint4 *>(stamp_row + b16);
-            const uint4 pv = *reinterpret_cast<const uint4 *>(pend_in + b16);
             const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w}, pw[4] = {pv.x, pv.y, pv.z, pv.w};
+            if (b16 + 16 < u1) {  // the next group's vectors are in flight while this one is classified
+                sv = *reinterpret_cast<const uint4 *>(stamp_row + b16 + 16);
+                pv = *reinterpret_cast<const uint4 *>(pend_in + b16 + 16);
+            }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
                 const int it = b16 + k;
@@ -474,7 +481,11 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const bool cls_cached = i1 - i0 <= kClsCap;
     int fl = 0;
     visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend) {
-        if (cls_cached) cls_sm[it - i0] = (uint8_t)(cls | (pend ? 4 : 0));
+        if (!cls_cached && cls == 0) cls = 1;
+        if (cls_cached) {
+            cls_sm[it - i0] = (uint8_t)(cls | (pend ? 4 : 0));
+            if (cls != 0) atomicOr(&nl_bits[(it - i0) >> 5], 1u << ((it - i0) & 31));
+        }
         fl |= (pend && cls != 0 ? 1 : 0) | (!pend && cls == 0 ? 2 : 0);
         pend_out[it] = cls == 0 ? (uint8_t)(pend + 1) : (uint8_t)0;
     });
@@ -489,6 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     __shared__ volatile int abort_sh;
     __shared__ long long wsum_sh[kThreads / 32];
     __shared__ int cut_sh[2];
+    __shared__ uint32_t nl_sh[kClsCap / 32];  // bit k: item i0 + k is not lazy
     __shared__ int flags_sh;  // bit 0: some item applies deferred idle ticks; bit 1: some item starts deferring
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -527,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     if (tid < 2) cut_sh[tid] = 0;
     if (tid == 0) flags_sh = 0;
     if (warp == kMmaWarp) tmem_alloc(&tmem_base_sh, a.tmem_cols);
-    split_items(a, wsum_sh, cut_sh, cls_sm, &flags_sh);
+    split_items(a, wsum_sh, cut_sh, cls_sm, &flags_sh, nl_sh);
     const int i0 = cut_sh[0], i1 = cut_sh[1];
     const int n_items = i1 - i0;
     const bool cls_cached = n_items <= kClsCap;
@@ -535,7 +547,16 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
-    auto cls_of = [&](int it) -> int { return cls_cached ? cls_sm[it - i0] & 3 : item_class(a, it); };
+    auto cls_of = [&](int it) -> int { return cls_cached ? cls_sm[it - i0] & 3 : max(item_class(a, it), 1); };
+    // First item at or after li (of this CTA) that is not lazy, n_items if none.
+    auto next_nl = [&](int li) -> int {
+        if (!cls_cached || li >= n_items) return min(li, n_items);
+        int w = li >> 5;
+        uint32_t m = nl_sh[w] & (0xFFFFFFFFu << (li & 31));
+        const int nw = (n_items + 31) >> 5;
+        while (m == 0u && ++w < nw) m = nl_sh[w];
+        return m ? (w << 5) + __ffs(m) - 1 : n_items;
+    };
     // Idle ticks deferred by item it before this tick (0 in the first tick after a reset).
     auto deferred_of = [&](int it) -> int {
         if (a.v0 || (cls_cached && !(cls_sm[it - i0] & 4))) return 0;
@@ -650,20 +671,12 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
         // split), and an idle item's operand is zero (its row and inputs are
         // known to be empty).  The row words of the next active item are
         // loaded one build ahead.
-        auto next_nl = [&](int li) -> int {
-            while (li < n_items && cls_at(li) == 0) ++li;
-            return li;
-        };
-        uint2 wnext = make_uint2(0u, 0u);
-        {
-            const int l0 = next_nl(0);
-            if (l0 < n_items && cls_at(l0) == 2) wnext = load_words(i0 + l0);
-        }
+        int lc = next_nl(0), lp = -1;  // item built in this iteration, item whose epilogue runs in it
+        uint2 wnext = lc < n_items && cls_at(lc) == 2 ? load_words(i0 + lc) : make_uint2(0u, 0u);
         int nb = 0;  // items whose operand this warp has built (operand and accumulator phases)
-        for (int li = 0; li <= n_items; ++li) {
-            if (cls_at(li) == 0 && cls_at(li - 1) == 0) continue;  // nothing to build, no epilogue
-            // Potentials of the epilogue item (li - 1), loaded before the build.
-            const int le = cls_at(li - 1) != 0 ? li - 1 : -1, ite = i0 + le;
+        while (lc < n_items || lp >= 0) {
+            // Potentials of the epilogue item lp, loaded before the build.
+            const int le = lp, ite = i0 + le;
             const int ce = ite / T, je = ite % T;
             uint4 vb[kPre][kVecs];
             auto vaddr = [&](int k) {  // this lane's first 16-byte vector of unit k
@@ -686,10 +699,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                         }
                 }
             }
-            // ---- (1) build S of item li
-            if (cls_at(li) != 0) {
-                const int it = i0 + li, c = it / T, j = it % T;
-                const bool act = cls_at(li) == 2;
+            // ---- (1) build S of item lc
+            if (lc < n_items) {
+                const int it = i0 + lc, c = it / T, j = it % T;
+                const bool act = cls_at(lc) == 2;
                 if (!wait(&s_free, (nb & 1) ^ 1)) break;
                 if (c != bc) {
                     if (has_task) odr = a.outdeg[(size_t)c * A + rax];
@@ -697,7 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 }
                 const uint2 wcur = wnext;
                 {
-                    const int ln = next_nl(li + 1);
+                    const int ln = next_nl(lc + 1);
                     wnext = ln < n_items && cls_at(ln) == 2 ? load_words(i0 + ln) : make_uint2(0u, 0u);
                 }
                 unsigned long long ev = 0;
@@ -730,10 +743,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
                 if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
             }
-            // ---- (2) epilogue of item li - 1
+            // ---- (2) epilogue of item lp
             if (le >= 0) {
-                // Items with an MMA before this one: nb counts those up to item li.
-                const int ne = nb - (cls_at(li) != 0 ? 1 : 0) - 1;
+                // Items with an MMA before this one: nb counts those up to item lc.
+                const int ne = nb - (lc < n_items ? 1 : 0) - 1;
                 const int buf = ne & 1;
                 if (ce != pc) {
                     const int4 pr = a.prm[(size_t)ce * N + n];  // leak, pos_thr, neg_thr, reset
@@ -872,6 +885,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     atomicAdd(cp + 2, (unsigned long long)n_out);
                 }
             }
+            lp = lc < n_items ? lc : -1;
+            lc = next_nl(lc + 1);
         }
     } else {
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kRegIssuer) : "memory");
@@ -881,12 +896,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
         uint32_t nw = 0, nd = 0;
         bool w_pending = false;
         const size_t vtile = (size_t)4 * N * 32 * sizeof(VT);
-        int na = 0;  // items issued
-        // The items that are not lazy, in order (as the workers visit them).
-        auto next_nl = [&](int li) -> int {
-            while (li < n_items && cls_of(i0 + li) == 0) ++li;
-            return li;
-        };
+        int na = 0;  // items issued, in the order the workers build them
         int lc = next_nl(0);
         int l1 = lc < n_items ? next_nl(lc + 1) : n_items;
         for (; lc < n_items; lc = l1, l1 = l1 < n_items ? next_nl(l1 + 1) : n_items) {
