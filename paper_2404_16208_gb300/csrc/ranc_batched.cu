@@ -611,8 +611,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
         // fan-in list [f0, f1) of the axon is kept for the current core.
         const bool has_in = a.tick < (long long)a.in_ticks;
         int fc = -1, f0 = 0, f1 = 0, ln0 = 0;
+        uint2 xnext = make_uint2(0u, 0u);  // first input line's words of the next item (ORed at its build)
         auto load_words = [&](int it) -> uint2 {
             const int c = it / T, j = it % T;
+            xnext = make_uint2(0u, 0u);
             if (!has_task) return make_uint2(0u, 0u);
             const uint2 *row = reinterpret_cast<const uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
             uint2 w = row[rax * 2 + rhf];
@@ -625,14 +627,12 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 }
                 if (f1 > f0) {
                     const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
-                    uint2 x = in[(size_t)ln0 * 2];
-                    for (int e = f0 + 1; e < f1; ++e) {
+                    xnext = in[(size_t)ln0 * 2];
+                    for (int e = f0 + 1; e < f1; ++e) {  // further lines (each waits for its load)
                         const uint2 y = in[(size_t)a.fin_line[e] * 2];
-                        x.x |= y.x;
-                        x.y |= y.y;
+                        w.x |= y.x;
+                        w.y |= y.y;
                     }
-                    w.x |= x.x;
-                    w.y |= x.y;
                 }
             }
             return w;
@@ -708,15 +708,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     if (has_task) odr = a.outdeg[(size_t)c * A + rax];
                     bc = c;
                 }
-                const uint2 wcur = wnext;
-                {
-                    const int ln = next_nl(lc + 1);
-                    wnext = ln < n_items && cls_at(ln) == 2 ? load_words(i0 + ln) : make_uint2(0u, 0u);
-                }
+                const uint2 wrow = wnext, wcur = make_uint2(wnext.x | xnext.x, wnext.y | xnext.y);
                 unsigned long long ev = 0;
                 if (has_task) {
                     uint2 *row = reinterpret_cast<uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
-                    if (act) row[rax * 2 + rhf] = make_uint2(0u, 0u);
+                    if (act && (wrow.x | wrow.y)) row[rax * 2 + rhf] = make_uint2(0u, 0u);
                     const int m0 = j * 128 + rhf * 64;
                     ev = (unsigned long long)odr * (unsigned)(__popc(wcur.x & valid_mask(a.n_valid, m0)) +
                                                                __popc(wcur.y & valid_mask(a.n_valid, m0 + 32)));
@@ -739,6 +735,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_full);
                 ++nb;
+                {
+                    const int ln = next_nl(lc + 1);
+                    if (ln < n_items && cls_at(ln) == 2) wnext = load_words(i0 + ln);
+                    else wnext = xnext = make_uint2(0u, 0u);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
                 if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
