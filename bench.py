@@ -36,13 +36,14 @@ PLAIN_SAMPLES, BATCH_SAMPLES = 10000, 4096
 L2_FLUSH_BYTES = 512 << 20
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one batched tick
-# launch from an ncu capture of a 1024-sample case, scaled by the number of
-# (core, tile) items to the 4096-sample launch; valid only for the tick kernel's
-# source it was taken on: the sha256 of ranc_batched.cu up to its helper-kernel
-# section (see profiles/batched_tick_kernel_mnist512_1024samples.md).
-PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "dad04dc78ecba147", "samples": 1024,
-                    "bytes_per_launch": 644.9e6}
+# DRAM traffic of the batched tick kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) per updated (sample, core) unit, from one ncu capture
+# of a tick in which every item of a 1024-sample case is updated; a launch's
+# traffic is that times the units it updates.  Valid only for the tick
+# kernel's source it was taken on: the sha256 of ranc_batched.cu up to its
+# helper-kernel section (see profiles/batched_tick_kernel_mnist512_1024samples.md).
+PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "b25ec0d7edde4120", "bytes": 393.698560e6 + 237.143040e6,
+                    "units": 1024 * 512}
 
 
 def kernel_source_sha():
@@ -51,10 +52,11 @@ def kernel_source_sha():
     return hashlib.sha256(src[:src.index("// Helper kernels: reset")].encode()).hexdigest()[:16]
 
 
-def profiled_traffic(n_samples):
+def profiled_traffic(units):
+    """DRAM bytes of a launch that updates units (sample, core) units."""
     if kernel_source_sha() != PROFILED_TRAFFIC["kernel_source_sha256_prefix"]:
         return None
-    return PROFILED_TRAFFIC["bytes_per_launch"] * n_samples / PROFILED_TRAFFIC["samples"]
+    return PROFILED_TRAFFIC["bytes"] / PROFILED_TRAFFIC["units"] * units
 
 
 def peaks():
@@ -237,6 +239,8 @@ def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
         ms += e0.elapsed_time(e1)
     launches = ranc.ranc_launch_count(sim.h) - l0
     cnt = ranc.ranc_read_counters(sim.h)
+    # item-ticks of the timed steps: updated, and deferred (potentials untouched)
+    upd, dfr = ranc.ranc_item_ticks(sim.h)
     ranc.ranc_set_kernel_timing(sim.h, True)
     run()
     kms, kn = ranc.ranc_read_kernel_timing(sim.h)
@@ -245,7 +249,8 @@ def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
     fmt = sim.potential_format()
     sim.close()
     return dict(ms=ms, samples=n_samples * steps, events=int(cnt[3]), launches=launches, kernel_ms=kms,
-                kernel_launches=kn, counts=counts, potential_format=fmt)
+                kernel_launches=kn, counts=counts, potential_format=fmt, item_ticks=(upd, dfr),
+                tick_launches=steps * WINDOW * -(-n_samples // sim.batch))
 
 
 def e2e_batched(ranc, torch, net, x, n_samples):
@@ -527,15 +532,20 @@ def main():
     fmt = br["potential_format"]
     vbytes = 4 if fmt == ranc.RANC_POTENTIAL_INT32 else 2  # this workload's range [-1032, 2047] fits fp16
     kavg_ms = br["kernel_ms"] / max(br["kernel_launches"], 1)
-    units = nb * net.n_cores
+    # Units a launch processes: (sample, core) pairs of the items it updates;
+    # an item whose tick is deferred reads and writes nothing (its potentials
+    # are brought up to date by a later update).
+    upd, dfr = br["item_ticks"]
+    units = upd * 128 / max(br["tick_launches"], 1)
     bytes_launch = batched_bytes_per_sample_core_tick(net, vbytes) * units
     achieved = bytes_launch / (kavg_ms * 1e-3) / 1e9
-    flops_launch = 2.0 * net.axons * net.neurons * (-(-nb // 128) * 128) * net.n_cores
+    flops_launch = 2.0 * net.axons * net.neurons * units  # crossbar product of the updated items (an idle one issues 1/16 of it)
     tflops = flops_launch / (kavg_ms * 1e-3) / 1e12
     roof = {"kernel": "batched_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(nb),
+            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(units),
             "peak_source": pk["source"] + " (hbm_gbs, of measured copy bandwidth)",
             "avg_launch_us": kavg_ms * 1e3, "bytes_per_launch": bytes_launch,
+            "sample_core_units_per_launch": units, "deferred_item_tick_frac": dfr / max(upd + dfr, 1),
             "tensor": {"achieved_tflops": tflops, "peak_tflops": pk["bf16_tflops_sustained"],
                        "frac": tflops / pk["bf16_tflops_sustained"], "kind": "tcgen05.mma kind::f16 (fp16, fp32 accumulate)"}}
     ekp = pr["kernel_ms"] / max(pr["kernel_launches"], 1)  # per tick

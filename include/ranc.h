@@ -258,6 +258,22 @@ int ranc_launch_count(const ranc_sim *sim, int64_t *launches);
  * by a replay.  Errors: RANC_EINVAL if a pointer is NULL. */
 int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays);
 
+/* Work of the batched path's tick kernel.  A work item is one core on one
+ * tile of 128 batch slots.  In each tick an item is either updated (its
+ * potentials are read and written; the crossbar product runs when its
+ * scheduler row or its core's input lines can hold spikes), or, when it
+ * receives no spike and every neuron of its core has leak <= 0, reset,
+ * theta- and v0 below theta+ and a saturating negative threshold
+ * (negative-threshold mode 0), its tick is deferred: such a tick can only
+ * take V to max(V + leak, theta-), k of them compose to
+ * max(V + k * leak, theta-) (Sec. II, Eq. 1-3 with no input), and that is
+ * applied before the item's next update or any state read, so every result
+ * is unchanged.  *updated and *deferred receive the item-ticks of each kind
+ * since ranc_create or the last ranc_reset (graph replays included).  The
+ * call synchronises the handle's stream.  Errors: RANC_EINVAL if a pointer is
+ * NULL; RANC_ESTATE on the plain path. */
+int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferred);
+
 /* How the handle stores the membrane potentials in device memory.  The paper
  * makes the potential's bit width a configuration parameter (Sec. III and
  * Sec. V); the library picks, at ranc_create, the narrowest storage that holds

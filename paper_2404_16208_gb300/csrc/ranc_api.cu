@@ -851,6 +851,18 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
     return RANC_OK;
 }
 
+extern "C" int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferred) {
+    CHECK_LIVE(sim);
+    if (!updated || !deferred) return RANC_EINVAL;
+    if (sim->path != RANC_PATH_BATCHED) return fail(sim, RANC_ESTATE, "item-ticks are counted on the batched path only");
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = batched_item_ticks(sim, h);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
+    *updated = (int64_t)h[0];
+    *deferred = (int64_t)h[1];
+    return RANC_OK;
+}
+
 extern "C" int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays) {
     if (!sim || !captures || !replays) return RANC_EINVAL;
     *captures = sim->graph_captures;

@@ -93,7 +93,8 @@ struct TickArgs {
     const uint8_t *core_flags; // [C] bit 0: some input line drives the core; bit 1: its idle ticks can be deferred
     const uint8_t *pend_in;    // [items] idle ticks deferred before this tick
     uint8_t *pend_out;         // [items] idle ticks deferred after this tick
-    int cost_active, cost_idle, cost_lazy, cost_wake;  // relative costs for the split of the items over the CTAs
+    int cost_active, cost_idle, cost_lazy, cost_wake, cost_first;  // relative costs for the split of the items over the CTAs
+    unsigned long long *item_ticks;  // [2]: items updated, items whose tick was deferred (accumulated)
 };
 
 constexpr int kPendMax = 250;  // deferred idle ticks of an item are applied before this many accumulate
@@ -376,18 +377,21 @@ __device__ __noinline__ void out_bus(const TickArgs &a, uint32_t olanes, uint32_
 // this tick); pend_out holds the deferred ticks after this tick of each of its
 // items; flags_sh bit 0 is set when some item applies deferred ticks in this
 // tick, bit 1 when some item starts deferring (its spike masks are cleared);
-// nl_bits has bit k set when item i0 + k is not lazy.  A range that does not
-// fit kClsCap defers nothing: its lazy items are updated as idle ones.
+// bit k of nl_bits[0] is set when item i0 + k is not lazy, of nl_bits[1]
+// when it starts deferring, of nl_bits[2] when it applies deferred ticks.  A
+// range that does not fit kClsCap defers nothing: its lazy items are updated
+// as idle ones (and only flags_sh and pend_out are written).
 __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, int *cut_sh, uint8_t *cls_sm,
-                                         int *flags_sh, uint32_t *nl_bits) {
+                                         int *flags_sh, uint32_t (*nl_bits)[kClsCap / 32]) {
     // The arguments this function reads, once (a reference to the kernel's
     // argument block is a generic pointer here: every field read would be a load).
     const uint8_t *const stamp_row = a.stamp_row, *const pend_in = a.pend_in, *const core_flags = a.core_flags;
     uint8_t *const pend_out = a.pend_out;
+    unsigned long long *const item_ticks = a.item_ticks;
     const int items = a.items, T = a.T;
     const bool all_active = a.all_active != 0, first = a.v0 != nullptr, inputs = a.tick < (long long)a.in_ticks;
     const uint8_t cycle = (uint8_t)(a.sclock >> 4);
-    const int c_act = a.cost_active, c_idle = a.cost_idle, c_lazy = a.cost_lazy, c_wake = a.cost_wake;
+    const int c_act = a.cost_active, c_idle = a.cost_idle, c_lazy = a.cost_lazy, c_wake = a.cost_wake, c_first = a.cost_first;
     // As class_from, on those copies.
     auto cls_from = [&](uint8_t stamp, uint8_t pend, uint8_t cflags) -> int {
         if (all_active || stamp == cycle || (inputs && (cflags & 1))) return 2;
@@ -400,7 +404,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const int per = ((items + kThreads - 1) / kThreads + 15) & ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t0 = min(items, tid * per), t1 = min(items, t0 + per);
-    for (int w = tid; w < kClsCap / 32; w += kThreads) nl_bits[w] = 0u;
+    for (int w = tid; w < 3 * kClsCap / 32; w += kThreads) nl_bits[w / (kClsCap / 32)][w % (kClsCap / 32)] = 0u;
     // fn(it, class, deferred idle ticks) for the items [u0, u1) of this thread.
     auto visit = [&](int u0, int u1, auto &&fn) {
         if (u0 >= u1) return;
@@ -432,7 +436,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     // Cost of an item: its class, plus the pass that applies deferred ticks
     // when it wakes up, plus the spike-mask clearing of a first lazy tick.
     auto cost_of = [&](int cls, int pend) -> int {
-        return (cls == 2 ? c_act : cls == 1 ? c_idle : c_lazy) + (cls != 0 && pend ? c_wake : 0) + (cls == 0 && !pend ? 1 : 0);
+        return (cls == 2 ? c_act : cls == 1 ? c_idle : c_lazy) + (cls != 0 && pend ? c_wake : 0) + (cls == 0 && !pend ? c_first : 0);
     };
     // Total cost of this thread's items.  A group of 16 items inside one core
     // is classified four at a time (bytes of the stamp and deferral vectors,
@@ -465,7 +469,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
                 n_lz0 += __popc(ml & ~mp) >> 3;
             }
             csum += (long long)c_act * n_act + (long long)c_idle * n_idle + (long long)c_lazy * n_lazy +
-                    (long long)c_wake * n_wake + n_lz0;
+                    (long long)c_wake * n_wake + (long long)c_first * n_lz0;
         }
     }
     long long cinc = csum;
@@ -511,17 +515,25 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     __syncthreads();
     const int i0 = cut_sh[0], i1 = cut_sh[1];
     const bool cls_cached = i1 - i0 <= kClsCap;
-    int fl = 0;
+    int fl = 0, n_up = 0, n_def = 0;
     visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend) {
         if (!cls_cached && cls == 0) cls = 1;
+        ++(cls != 0 ? n_up : n_def);
         if (cls_cached) {
-            cls_sm[it - i0] = (uint8_t)(cls | (pend ? 4 : 0));
-            if (cls != 0) atomicOr(&nl_bits[(it - i0) >> 5], 1u << ((it - i0) & 31));
+            const int k = it - i0;
+            cls_sm[k] = (uint8_t)(cls | (pend ? 4 : 0));
+            if (cls != 0) atomicOr(&nl_bits[0][k >> 5], 1u << (k & 31));
+            if (cls == 0 && !pend) atomicOr(&nl_bits[1][k >> 5], 1u << (k & 31));
+            if (cls != 0 && pend) atomicOr(&nl_bits[2][k >> 5], 1u << (k & 31));
         }
         fl |= (pend && cls != 0 ? 1 : 0) | (!pend && cls == 0 ? 2 : 0);
         pend_out[it] = cls == 0 ? (uint8_t)(pend + 1) : (uint8_t)0;
     });
     if (fl) atomicOr(flags_sh, fl);
+    n_up = __reduce_add_sync(0xffffffffu, n_up);
+    n_def = __reduce_add_sync(0xffffffffu, n_def);
+    if (lane == 0 && n_up) atomicAdd(item_ticks, (unsigned long long)n_up);
+    if (lane == 0 && n_def) atomicAdd(item_ticks + 1, (unsigned long long)n_def);
 }
 
 template <typename VT, int kNegReset>
@@ -532,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     __shared__ volatile int abort_sh;
     __shared__ long long wsum_sh[kThreads / 32];
     __shared__ int cut_sh[2];
-    __shared__ uint32_t nl_sh[kClsCap / 32];  // bit k: item i0 + k is not lazy
+    __shared__ uint32_t nl_sh[3][kClsCap / 32];  // bit k: item i0 + k is not lazy / starts deferring / wakes up
     __shared__ int flags_sh;  // bit 0: some item applies deferred idle ticks; bit 1: some item starts deferring
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -584,9 +596,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     auto next_nl = [&](int li) -> int {
         if (!cls_cached || li >= n_items) return min(li, n_items);
         int w = li >> 5;
-        uint32_t m = nl_sh[w] & (0xFFFFFFFFu << (li & 31));
+        uint32_t m = nl_sh[0][w] & (0xFFFFFFFFu << (li & 31));
         const int nw = (n_items + 31) >> 5;
-        while (m == 0u && ++w < nw) m = nl_sh[w];
+        while (m == 0u && ++w < nw) m = nl_sh[0][w];
         return m ? (w << 5) + __ffs(m) - 1 : n_items;
     };
     // Idle ticks deferred by item it before this tick (0 in the first tick after a reset).
@@ -674,10 +686,14 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
         // Items that are updated in this tick after deferring idle ticks: the
         // deferred ticks are applied first, each thread to the potentials that
         // its own epilogue reads later (program order, no barrier needed).
-        if (flags_sh & 1)
-            for (int li = 0; li < n_items; ++li) {
-                const int it = i0 + li, pe = cls_at(li) != 0 ? deferred_of(it) : 0;
-                if (!pe) continue;
+        // fn(li) for every set bit li of bitmap b (the items of this CTA).
+        auto for_bits = [&](const uint32_t *b, auto &&fn) {
+            for (int w = 0; w < (n_items + 31) >> 5; ++w)
+                for (uint32_t m = b[w]; m; m &= m - 1u) fn((w << 5) + __ffs(m) - 1);
+        };
+        auto wake = [&](int li) {
+            const int it = i0 + li, pe = cls_at(li) != 0 ? deferred_of(it) : 0;
+            if (pe) {
                 const int c = it / T, j = it % T;
                 const int4 pr = a.prm[(size_t)c * N + n];
                 for (int k = 0; k < nu; ++k) {
@@ -690,14 +706,18 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     for (int e = 0; e < kVecs; ++e) vp[e * 32] = q[e];
                 }
             }
+        };
+        if (flags_sh & 1) {
+            if (cls_cached) for_bits(nl_sh[2], wake);
+            else for (int li = 0; li < n_items; ++li) wake(li);
+        }
         // Items that start deferring in this tick: their spike masks are zero
         // (and stay so while they keep deferring).
         if (flags_sh & 2)
-            for (int li = 0; li < n_items; ++li)
-                if (cls_at(li) == 0 && deferred_of(i0 + li) == 0) {
-                    const int it = i0 + li, c = it / T, j = it % T;
-                    for (int k = 0; k < nu; ++k) a.spk[(((size_t)j * C + c) * 4 + cc0 + k) * N + n] = 0u;
-                }
+            for_bits(nl_sh[1], [&](int li) {
+                const int it = i0 + li, c = it / T, j = it % T;
+                for (int k = 0; k < nu; ++k) a.spk[(((size_t)j * C + c) * 4 + cc0 + k) * N + n] = 0u;
+            });
         // Iteration li builds the operand of item li and runs the epilogue of
         // item li - 1; lazy items take neither (their tick is recorded by the
         // split), and an idle item's operand is zero (its row and inputs are
@@ -1142,11 +1162,13 @@ struct Batched {
     // Item activity: delivery stamps [16][spitch], deferred idle ticks
     // [2][spitch] (double-buffered by tick parity), per-core flags.
     uint8_t *stamp = nullptr, *pend = nullptr, *core_flags = nullptr;
+    unsigned long long *item_ticks = nullptr;  // [2] updated / deferred item-ticks since the last counter reset
     long long spitch = 0;
     bool any_lazy = false;
-    // Relative cost of an active, idle and lazy item and of applying deferred
-    // ticks (the split of a tick's items over the CTAs balances their sum).
-    int cost_active = 16, cost_idle = 16, cost_lazy = 1, cost_wake = 10;
+    // Relative cost of an active, idle and lazy item, of applying deferred
+    // ticks and of a lazy item's first tick (which clears its spike masks);
+    // the split of a tick's items over the CTAs balances their sum.
+    int cost_active = 64, cost_idle = 56, cost_lazy = 1, cost_wake = 40, cost_first = 5;
     CUtensorMap wmap;  // 64-byte aligned by its declaration
 };
 
@@ -1272,7 +1294,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         dev_alloc((void **)&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess ||
         dev_alloc((void **)&bs->stamp, (size_t)kRows * bs->spitch) != cudaSuccess ||
         dev_alloc((void **)&bs->pend, (size_t)2 * bs->spitch) != cudaSuccess ||
-        dev_alloc((void **)&bs->core_flags, (size_t)C) != cudaSuccess) {
+        dev_alloc((void **)&bs->core_flags, (size_t)C) != cudaSuccess || dev_alloc((void **)&bs->item_ticks, 16) != cudaSuccess) {
         why = "device allocation of the batched state failed";
         return cudaErrorMemoryAllocation;
     }
@@ -1283,7 +1305,8 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         (e = cudaMemcpy(bs->fin_line, fline.data(), fline.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(bs->core_flags, cfl.data(), (size_t)C, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(bs->stamp, 0, (size_t)kRows * bs->spitch)) != cudaSuccess ||
-        (e = cudaMemset(bs->pend, 0, (size_t)2 * bs->spitch)) != cudaSuccess) {
+        (e = cudaMemset(bs->pend, 0, (size_t)2 * bs->spitch)) != cudaSuccess ||
+        (e = cudaMemset(bs->item_ticks, 0, 16)) != cudaSuccess) {
         why = "copy of the batched network arrays";
         return e;
     }
@@ -1345,6 +1368,8 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.pend_in = bs->pend + (size_t)(sim->tick & 1) * bs->spitch;
     a.pend_out = bs->pend + (size_t)((sim->tick + 1) & 1) * bs->spitch;
     a.cost_active = bs->cost_active; a.cost_idle = bs->cost_idle; a.cost_lazy = bs->cost_lazy; a.cost_wake = bs->cost_wake;
+    a.cost_first = bs->cost_first;
+    a.item_ticks = bs->item_ticks;
     const int grid = std::min(bs->n_sm, a.items);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
@@ -1426,7 +1451,14 @@ cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
     }
     if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B_pad * sim->n_outputs * 4, sim->stream)) != cudaSuccess) return e;
     if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
+    if (counters && (e = cudaMemsetAsync(B_of(sim)->item_ticks, 0, 16, sim->stream)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// Updated and deferred item-ticks since the last counter reset (synchronises the stream).
+cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host2) {
+    cudaError_t e = cudaMemcpyAsync(host2, B_of(sim)->item_ticks, 16, cudaMemcpyDeviceToHost, sim->stream);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(sim->stream);
 }
 
 // Makes the transposed-input buffer hold n_ticks ticks (may synchronise the
@@ -1552,7 +1584,7 @@ cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, u
 void batched_teardown(ranc_sim *sim) {
     Batched *bs = B_of(sim);
     if (!bs) return;
-    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT, bs->stamp, bs->pend, bs->core_flags};
+    void *ptrs[] = {bs->wfold, bs->fin_ptr, bs->fin_line, bs->outdeg, bs->inT, bs->stamp, bs->pend, bs->core_flags, bs->item_ticks};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete bs;

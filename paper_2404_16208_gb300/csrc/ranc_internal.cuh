@@ -200,6 +200,7 @@ cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cu
 cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
 cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
+cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host2);
 cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, uint32_t *spk_canon,
                                   uint32_t *ring_canon);

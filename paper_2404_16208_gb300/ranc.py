@@ -23,7 +23,7 @@ EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_read_core_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
-            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_potential_format", "ranc_destroy",
+            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_item_ticks", "ranc_potential_format", "ranc_destroy",
             "ranc_last_error")
 RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
 
@@ -75,6 +75,7 @@ def load_library(path=LIB_PATH):
         "ranc_read_kernel_timing": ([vp, C.POINTER(C.c_double), C.POINTER(i64)], C.c_int),
         "ranc_launch_count": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_graph_stats": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "ranc_item_ticks": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_potential_format": ([vp, C.POINTER(i32)], C.c_int),
         "ranc_destroy": ([vp], None),
         "ranc_last_error": ([vp], C.c_char_p),
@@ -240,6 +241,13 @@ def ranc_launch_count(h):
     n = C.c_int64()
     _check(_lib.ranc_launch_count(h, C.byref(n)), h)
     return n.value
+
+
+def ranc_item_ticks(h):
+    """(updated, deferred) item-ticks of the batched tick kernel."""
+    u, d = C.c_int64(), C.c_int64()
+    _check(_lib.ranc_item_ticks(h, C.byref(u), C.byref(d)), h)
+    return u.value, d.value
 
 
 def ranc_graph_stats(h):

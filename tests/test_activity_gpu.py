@@ -103,7 +103,27 @@ def test_idle_and_deferred_ticks_read_in_chunks(ranc, oracle_mod, fmt):
         check_state(sim, ref, t - 1, f"(chunks, format {fmt})")
     np.testing.assert_array_equal(sim.outputs(), ref["out"])
     np.testing.assert_array_equal(sim.counters()[:4], ref["counters"][:, :4].sum(0))
+    # every (core, 128-sample tile) item is either updated or deferred in every tick,
+    # and this workload defers some
+    upd, dfr = ranc.ranc_item_ticks(sim.h)
+    assert upd + dfr == -(-B // 128) * net.n_cores * T and dfr > 0
     sim.close()
+
+
+def test_item_ticks_without_deferral_and_on_the_plain_path(ranc, oracle_mod):
+    net = lazy_net(96, hot_cores=range(6))  # every core has a positive leak somewhere: nothing defers
+    x = with_gap(W.rate_coded_inputs(41, 130, 10, net.n_inputs, 0.3), 2, 8)
+    ref = oracle_mod.run(net, x, 16, n_threads=NPROC)
+    sim = ranc.Sim(net, 130, ranc.RANC_PATH_BATCHED)
+    sim.load_inputs(x)
+    sim.step(16)
+    np.testing.assert_array_equal(sim.outputs(), ref["out"])
+    assert ranc.ranc_item_ticks(sim.h) == (2 * net.n_cores * 16, 0)
+    sim.close()
+    plain = ranc.Sim(net, 1, ranc.RANC_PATH_PLAIN)
+    with pytest.raises(ranc.RancError):
+        ranc.ranc_item_ticks(plain.h)
+    plain.close()
 
 
 def test_state_read_every_tick_through_idle_periods(ranc, oracle_mod):
