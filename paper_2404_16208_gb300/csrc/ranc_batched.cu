@@ -127,9 +127,6 @@ __device__ __forceinline__ int item_class(const TickArgs &a, int it) {
     return class_from(a, a.stamp_row[it], a.pend_in[it], a.core_flags[it / a.T]);
 }
 
-__device__ __forceinline__ int class_cost(const TickArgs &a, int cls) {
-    return cls == 2 ? a.cost_active : cls == 1 ? a.cost_idle : a.cost_lazy;
-}
 
 // ---------------------------------------------------------------------------
 // tcgen05 / TMA wrappers (inline PTX)
@@ -346,26 +343,6 @@ __device__ __forceinline__ size_t v_index(int j, int c, int cc, int n, int i, in
 // ---------------------------------------------------------------------------
 // The tick kernel
 // ---------------------------------------------------------------------------
-
-// Output-bus events of one warp's 32-sample unit: one warp-wide pass per
-// output neuron that fired (olanes: the lanes holding one); lane i adds sample
-// bs = (first sample of the unit) + i, so no lane loops over spikes.
-__device__ __noinline__ void out_bus(const TickArgs &a, uint32_t olanes, uint32_t live, uint32_t id, int bs) {
-    const int lane = threadIdx.x & 31;
-    uint32_t *const out = a.out, *const olog = a.olog;
-    const int n_out = a.n_out, olog_rows = a.olog_rows;
-    const long long olog_stride = a.olog_stride;
-    while (olanes) {
-        const int L = __ffs(olanes) - 1;
-        olanes &= olanes - 1u;
-        const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
-        const uint32_t idL = __shfl_sync(0xffffffffu, id, L);
-        if ((mL >> lane) & 1u) {
-            atomicAdd(out + (size_t)bs * n_out + idL, 1u);
-            if (olog && bs < olog_rows) atomicAdd(olog + (size_t)bs * olog_stride + idL, 1u);
-        }
-    }
-}
 
 // Split of one tick's items over the CTAs, run by every thread of a CTA at
 // kernel start (kept out of line so that it does not weigh on the register
