@@ -798,6 +798,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 tc_fence_after();
                 const uint32_t kind = dest_kind(dd);
                 uint32_t n_sp = 0, n_pk = 0, n_out = 0;
+                uint32_t dm0 = 0u, dm1 = 0u;  // spike masks of the two units (delivered together when nu == 2)
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (k >= nu) break;
@@ -878,14 +879,17 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     const uint32_t live = mask & valid;
                     n_sp += __popc(live);
                     if (mask && kind == RANC_DEST_CORE) {
-                        const uint32_t ax = dest_axon(dd);
-                        const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
-                        atomicOr(reinterpret_cast<uint32_t *>(a.ring) + ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
-                                 mask);
                         n_pk += __popc(live);
-                        // The destination row's stamp: the cycle of the tick that reads it.
-                        a.stamp[(size_t)r * a.spitch + (size_t)dd.x * T + je] = (uint8_t)((a.sclock + dest_delay(dd)) >> 4);
+                        if (nu == 1) {
+                            const uint32_t ax = dest_axon(dd);
+                            const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
+                            atomicOr(reinterpret_cast<uint32_t *>(a.ring) + ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
+                                     mask);
+                            // The destination row's stamp: the cycle of the tick that reads it.
+                            a.stamp[(size_t)r * a.spitch + (size_t)dd.x * T + je] = (uint8_t)((a.sclock + dest_delay(dd)) >> 4);
+                        }
                     }
+                    (k == 0 ? dm0 : dm1) = mask;
                     // Output bus: one warp-wide pass per output neuron that fired;
                     // lane i adds sample cc*32 + i, so no lane loops over spikes.
                     uint32_t olanes = __ballot_sync(0xffffffffu, kind == RANC_DEST_OUTPUT && live != 0u);
@@ -905,6 +909,16 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                // Two units of one neuron: adjacent words (cc0 even) of the same
+                // destination row, delivered by one 64-bit atomicOr, one stamp.
+                if (nu == 2 && kind == RANC_DEST_CORE && (dm0 | dm1)) {
+                    const uint32_t ax = dest_axon(dd);
+                    const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
+                    atomicOr(reinterpret_cast<unsigned long long *>(reinterpret_cast<uint32_t *>(a.ring) +
+                                                                    ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc0),
+                             ((unsigned long long)dm1 << 32) | dm0);
+                    a.stamp[(size_t)r * a.spitch + (size_t)dd.x * T + je] = (uint8_t)((a.sclock + dest_delay(dd)) >> 4);
+                }
                 n_sp = __reduce_add_sync(0xffffffffu, n_sp);
                 n_pk = __reduce_add_sync(0xffffffffu, n_pk);
                 n_out = __reduce_add_sync(0xffffffffu, n_out);
