@@ -10,17 +10,25 @@
 // integer below 2^22 in magnitude, so fp32 accumulation in tensor memory is
 // exact and the result equals the integer sum of the CPU definition.
 //
-// Roles inside one CTA (544 threads, one CTA per SM, persistent over items):
-//   warps 0-15  workers.  Iteration i: (1) read and clear the scheduler row of
-//               tick t for item i and expand its bits to the fp16 0/1 operand
-//               S (sample-contiguous, 128-byte swizzled: a scheduler word is
-//               already 32 consecutive samples of one axon, so no transpose);
-//               (2) epilogue of item i-1 while the tensor core works on item
-//               i: tensor memory -> registers (tcgen05.ld), potential update
-//               (leak, thresholds, reset), spike masks over 32 samples per
-//               neuron, delivery with one atomicOr per (neuron, 32 samples)
-//               into the sample-minor scheduler rows, output-bus counts;
-//   warp 16     tensor-memory allocation, TMA loads of the folded weights of
+// Roles inside one CTA (640 threads, one CTA per SM, persistent over items):
+//   all         the split (split_items): every item of the tick is classified
+//               active / idle / lazy (see item_class) and the CTA takes its
+//               share of the items by a cost prefix computed in every CTA;
+//   warps 0-15  workers (104 registers after setmaxnreg).  Iteration i over
+//               the CTA's items that are not lazy: (1) read and clear the
+//               scheduler row of tick t for item i (loaded one build ahead)
+//               and expand its bits to the fp16 0/1 operand S
+//               (sample-contiguous, 128-byte swizzled: a scheduler word is
+//               already 32 consecutive samples of one axon, so no transpose;
+//               zero for an idle item); (2) epilogue of item i-1 while the
+//               tensor core works on item i: tensor memory -> registers
+//               (tcgen05.ld), potential update (leak, thresholds, reset),
+//               spike masks over 32 samples per neuron, delivery of a
+//               neuron's spike masks with one atomicOr into the sample-minor
+//               scheduler rows (and the destination row's stamp), output-bus
+//               counts;
+//   warps 16-19 one warpgroup (48 registers after setmaxnreg); warp 16:
+//               tensor-memory allocation, TMA loads of the folded weights of
 //               the current core (cp.async.bulk.tensor, 128-byte swizzle),
 //               L2 prefetch of the next items' potentials and rows,
 //               tcgen05.mma issue and commit.
@@ -39,6 +47,9 @@
 //   ring  [T][C][16][A][4]   scheduler rows: word k of axon a holds samples 32k..32k+31
 //   spk   [T][C][4][N]       spike masks of the last tick (32 samples per word)
 //   inT   [T][ticks][Lpad][4] input lines, same sample-minor packing
+//   stamp [16][items]        per scheduler row and item (item it = c*T + j): the
+//                            cycle of the tick that reads the row, written on delivery
+//   pend  [2][items]         deferred idle ticks per item (by tick parity)
 
 #include <cuda.h>
 #include <cuda_fp16.h>
