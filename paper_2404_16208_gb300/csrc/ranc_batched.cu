@@ -749,13 +749,13 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     bc = c;
                 }
                 const uint2 wrow = wnext, wcur = make_uint2(wnext.x | xnext.x, wnext.y | xnext.y);
-                unsigned long long ev = 0;
+                // Synaptic events of the item: spikes x out-degree, at most 32 * 64 * 256 per warp.
+                uint32_t ev = 0u;
                 if (has_task) {
                     uint2 *row = reinterpret_cast<uint2 *>(a.ring + (((size_t)j * C + c) * kRows + r0) * A);
                     if (act && (wrow.x | wrow.y)) row[rax * 2 + rhf] = make_uint2(0u, 0u);
                     const int m0 = j * 128 + rhf * 64;
-                    ev = (unsigned long long)odr * (unsigned)(__popc(wcur.x & valid_mask(a.n_valid, m0)) +
-                                                               __popc(wcur.y & valid_mask(a.n_valid, m0 + 32)));
+                    ev = odr * (uint32_t)(__popc(wcur.x & valid_mask(a.n_valid, m0)) + __popc(wcur.y & valid_mask(a.n_valid, m0 + 32)));
                     // Row rax of the 64-sample half rhf: 8 chunks of 8 samples
                     // (16 bytes), chunk position XOR the row within its 8-axon
                     // group (128-byte swizzle).  The two halves write their
@@ -780,9 +780,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     if (ln < n_items && cls_at(ln) == 2) wnext = load_words(i0 + ln);
                     else wnext = xnext = make_uint2(0u, 0u);
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-                if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, ev);
+                ev = __reduce_add_sync(0xffffffffu, ev);
+                if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * C + c) * 4 + 3, (unsigned long long)ev);
             }
             // ---- (2) epilogue of item lp
             if (le >= 0) {
