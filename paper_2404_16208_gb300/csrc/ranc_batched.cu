@@ -606,9 +606,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     if (warp < kWorkers) {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kRegWorker) : "memory");
         // ------------------------------------------------------------ workers
-        // Iteration li: (1) build the operand tile S of item li (the tensor
-        // core is idle, waiting for it); (2) epilogue of item li-1 while the
-        // tensor core works on item li.
+        // Each iteration, over the CTA's items that are not lazy: (1) build
+        // the operand tile S of item lc (the tensor core is idle, waiting for
+        // it); (2) epilogue of the previous such item lp while the tensor core
+        // works on item lc.
         //
         // Epilogue units: (neuron half h, 32-sample chunk cc).  Warp (q, g)
         // owns TMEM lanes 32q..32q+31 and units of one neuron
@@ -706,11 +707,10 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 const int it = i0 + li, c = it / T, j = it % T;
                 for (int k = 0; k < nu; ++k) a.spk[(((size_t)j * C + c) * 4 + cc0 + k) * N + n] = 0u;
             });
-        // Iteration li builds the operand of item li and runs the epilogue of
-        // item li - 1; lazy items take neither (their tick is recorded by the
-        // split), and an idle item's operand is zero (its row and inputs are
-        // known to be empty).  The row words of the next active item are
-        // loaded one build ahead.
+        // Lazy items take neither a build nor an epilogue (their tick is
+        // recorded by the split); an idle item's operand is zero (its row and
+        // inputs are known to be empty).  The row words of the next active
+        // item are loaded right after each build, one build ahead.
         int lc = next_nl(0), lp = -1;  // item built in this iteration, item whose epilogue runs in it
         uint2 wnext = lc < n_items && cls_at(lc) == 2 ? load_words(i0 + lc) : make_uint2(0u, 0u);
         int nb = 0;  // items whose operand this warp has built (operand and accumulator phases)
