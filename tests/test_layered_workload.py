@@ -70,3 +70,48 @@ def test_layered_net_cores_fall_idle_and_wake_up(oracle_mod):
     assert idle.sum() > 0.2 * idle.size  # a good share of core-ticks is idle
     wakeups = idle[:-1] & ~idle[1:]
     assert wakeups.sum() >= 2  # and idle cores receive input again
+
+
+def test_idle_ticks_of_eligible_cores_compose_in_closed_form(oracle_mod):
+    """The identity behind the batched path's deferred ticks, checked on the
+    oracle's trace: over a run of ticks in which a core receives no packet and
+    no input, every neuron of a core with leak <= 0, reset, theta- and v0
+    below theta+ and a saturating negative threshold does not fire, and its
+    potential after k such ticks is max(V + k * leak, theta-)."""
+    net = W.layered_net(57, layers=(2, 2, 2), w_lim=60, pthr=(1, 150), nthr=(-150, -1))
+    T = 34
+    x = W.rate_coded_inputs(23, 48, 20, net.n_inputs, 0.35)
+    x[:, 3:14] = 0  # a long input gap
+    ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
+    v, sp = ref["v_trace"], ref["spike_trace"]  # [S, T, C, N]
+    dc = _dest_cores(net)
+    # per (sample, tick, core): a packet or an input arrives
+    S = x.shape[0]
+    recv = np.zeros((S, T, net.n_cores), bool)
+    for t in range(T):
+        for s, c, n in zip(*np.nonzero(sp[:, t])):
+            if dc[c, n] >= 0 and t + int(net.dest["delay"][c, n]) < T:
+                recv[s, t + int(net.dest["delay"][c, n]), dc[c, n]] = True
+    bits = np.unpackbits(x.view(np.uint8), axis=-1, bitorder="little")[..., :net.n_inputs]  # [S, T_in, L]
+    offs = np.asarray(net.in_offsets)
+    for line in range(net.n_inputs):
+        for e in range(offs[line], offs[line + 1]):
+            recv[:, :x.shape[1], net.in_core[e]] |= bits[:, :, line].astype(bool)
+    lam = net.leak.astype(np.int64)
+    checked = 0
+    for s in range(S):
+        for c in range(net.n_cores):
+            t = 1
+            while t < T:
+                if recv[s, t, c]:
+                    t += 1
+                    continue
+                t1 = t  # ticks t1 .. t2 - 1 receive nothing
+                while t < T and not recv[s, t, c]:
+                    t += 1
+                k = t - t1
+                assert not sp[s, t1:t, c].any()
+                expect = np.maximum(v[s, t1 - 1, c].astype(np.int64) + k * lam[c], net.neg_thr[c])
+                np.testing.assert_array_equal(v[s, t - 1, c], expect, err_msg=f"sample {s} core {c} ticks {t1}..{t - 1}")
+                checked += k
+    assert checked > 500  # idle ticks covered
