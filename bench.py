@@ -76,11 +76,24 @@ class Clocks:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index, self.rows, self.proc = index, [], None
+        self.index, self.rows, self.proc = self.smi_id(index), [], None
+
+    @staticmethod
+    def smi_id(index):
+        """nvidia-smi's name for torch's device `index`: its UUID (CUDA's
+        ordinals and nvidia-smi's may differ, e.g. under CUDA_VISIBLE_DEVICES)."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(index).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [v.strip() for v in vis.split(",") if v.strip()]
+            return ids[index] if index < len(ids) else str(index)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -139,6 +152,7 @@ def oracle_rate(net, x_all, budget_s=12.0, threads=None):
     r = oracle.run(net, x_all[:n], WINDOW, n_threads=threads)
     dt = time.perf_counter() - t0
     total_s, total_n, events = dt, n, int(r["counters"][:, 3].sum())
+    outs = [r["out"]]
     more = int(min(x_all.shape[0] - n, max(0, (budget_s - dt) / max(dt / n, 1e-9))))
     if more > 0:
         t0 = time.perf_counter()
@@ -146,8 +160,9 @@ def oracle_rate(net, x_all, budget_s=12.0, threads=None):
         total_s += time.perf_counter() - t0
         total_n += more
         events += int(r["counters"][:, 3].sum())
+        outs.append(r["out"])
     return dict(samples=total_n, seconds=total_s, samples_per_s=total_n / total_s, events_per_s=events / total_s,
-                threads=threads)
+                threads=threads, out=np.concatenate(outs))
 
 
 def flush_l2(buf):
@@ -208,26 +223,68 @@ POTENTIAL_DTYPE = {
     2: "fp16 potentials (integers <= 2048, exact); fp16 0/1 and weight operands, fp32 accumulate (all exact)"}
 
 
-def batched_bytes_per_sample_core_tick(net, vbytes):
-    """Algorithmic bytes per (sample, core, tick) of the batched tick kernel:
-    the potential read and written once, the scheduler row read and cleared,
-    the spike mask recorded.  Weights and parameters are amortised over 4096
-    samples and left out."""
+def batched_bytes_per_sample_core_tick(net, vbytes, active=True):
+    """Algorithmic bytes per updated (sample, core, tick) unit of the batched
+    tick kernel: the potential read and written once and the spike mask
+    recorded; an active unit also reads and clears its scheduler row (an idle
+    one is known to have an empty row and reads none).  Weights and
+    parameters are amortised over the samples and left out."""
     A, N = net.axons, net.neurons
-    return 2 * N * vbytes + 2 * A // 8 + N // 8
+    return 2 * N * vbytes + N // 8 + (2 * A // 8 if active else 0)
+
+
+def measure_l2_copy(torch, mib=16, reps=200):
+    """Copy bandwidth of a working set that stays in L2 (two buffers of `mib`
+    MiB, read + write bytes), CUDA events: the ceiling for a kernel whose
+    state is L2-resident."""
+    a = torch.ones(mib << 18, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    e1.synchronize()
+    return 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+def oracle_outputs(net, x, n):
+    """Output-bus counts of the first n samples, from the CPU oracle."""
+    import oracle
+    oracle.build()
+    return oracle.run(net, x[:n], WINDOW, n_threads=os.cpu_count() or 1)["out"]
+
+
+def parity_check(ref, **runs):
+    """Bit-for-bit comparison of each run's first len(ref) output-bus counts
+    with the oracle's."""
+    n = ref.shape[0]
+    res = {"compared": "output-bus counts per (sample, id) vs the CPU oracle", "samples": int(n)}
+    for name, c in runs.items():
+        res[name] = bool(np.array_equal(np.asarray(c)[:n].view(np.uint32), ref.astype(np.uint32)))
+    res["equal"] = all(res[k] for k in runs)
+    return res
 
 
 def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
     """Batched path: one handle of n_samples; a step is one sample window
-    (reset, input transposition, 24 ticks, output copy) on the device."""
+    (reset, input transposition, 24 ticks, output copy) on the device, one
+    replay of the window graph.  With kernel timing on, the recorded graph
+    brackets its 24 tick launches with an event pair, so the tick kernels'
+    time comes from the timed replays themselves (folded after each step,
+    outside the timed region)."""
     sim = ranc.Sim(net, n_samples, ranc.RANC_PATH_BATCHED)
     dout = torch.zeros((n_samples, net.n_outputs), dtype=torch.int32, device="cuda")
     run = lambda: ranc.ranc_run_samples(sim.h, dx.data_ptr(), n_samples, T_IN, WINDOW, dout.data_ptr(),
                                         ranc.RANC_MEM_DEVICE)
+    ranc.ranc_set_kernel_timing(sim.h, True)
     for _ in range(warmup):
         run()
     torch.cuda.synchronize()
     ranc.ranc_reset(sim.h)
+    ranc.ranc_set_kernel_timing(sim.h, True)  # totals from zero
     l0 = ranc.ranc_launch_count(sim.h)
     ms = 0.0
     for _ in range(steps):
@@ -237,20 +294,21 @@ def bench_batched(ranc, torch, net, dx, n_samples, steps, warmup):
         e1.record()
         e1.synchronize()
         ms += e0.elapsed_time(e1)
+        ranc.ranc_read_kernel_timing(sim.h)  # folds this replay's event pair
     launches = ranc.ranc_launch_count(sim.h) - l0
-    cnt = ranc.ranc_read_counters(sim.h)
-    # item-ticks of the timed steps: updated, and deferred (potentials untouched)
-    upd, dfr = ranc.ranc_item_ticks(sim.h)
-    ranc.ranc_set_kernel_timing(sim.h, True)
-    run()
     kms, kn = ranc.ranc_read_kernel_timing(sim.h)
     ranc.ranc_set_kernel_timing(sim.h, False)
-    counts = dout.cpu().numpy()
+    cnt = ranc.ranc_read_counters(sim.h)
+    # item-ticks of the timed steps: active (row and inputs read), idle (no
+    # synaptic input) and deferred (potentials untouched in that tick)
+    act, idle, dfr = ranc.ranc_item_classes(sim.h)
+    captures, replays = ranc.ranc_graph_stats(sim.h)
+    counts = dout.cpu().numpy().view(np.uint32)
     fmt = sim.potential_format()
     sim.close()
     return dict(ms=ms, samples=n_samples * steps, events=int(cnt[3]), launches=launches, kernel_ms=kms,
-                kernel_launches=kn, counts=counts, potential_format=fmt, item_ticks=(upd, dfr),
-                tick_launches=steps * WINDOW * -(-n_samples // sim.batch))
+                kernel_launches=kn, counts=counts, potential_format=fmt, item_classes=(act, idle, dfr),
+                graph=(captures, replays), tick_launches=steps * WINDOW * -(-n_samples // sim.batch))
 
 
 def e2e_batched(ranc, torch, net, x, n_samples):
@@ -265,7 +323,7 @@ def e2e_batched(ranc, torch, net, x, n_samples):
         ranc.ranc_run_samples(sim.h, xh, n_samples, T_IN, WINDOW, ch)
     dt = (time.perf_counter() - t0) / reps
     sim.close()
-    return dict(value=n_samples / dt, h2d=int(xh.nbytes), d2h=int(ch.nbytes))
+    return dict(value=n_samples / dt, h2d=int(xh.nbytes), d2h=int(ch.nbytes), counts=ch.copy())
 
 
 def bench_truenorth(ranc, torch, steps, warmup):
@@ -523,9 +581,12 @@ def main():
     if "plain" not in legs:
         samples = br["samples"] * ws
         if rank == 0:
+            par = parity_check(oracle_outputs(net, x, 16), batched=br["counts"])
             print(json.dumps({"metric": METRIC, "value": samples / (ms_b * 1e-3), "unit": "samples/s",
                               "legs": "batched only (profiling case)", "samples_per_step": nb,
-                              "ms_per_step": ms_b / args.steps}))
+                              "ms_per_step": ms_b / args.steps, "parity": par}))
+            if not par["equal"]:
+                sys.exit(1)
         return
 
     # Roofline of the dominant kernel (the batched tick kernel).
@@ -534,36 +595,54 @@ def main():
     kavg_ms = br["kernel_ms"] / max(br["kernel_launches"], 1)
     # Units a launch processes: (sample, core) pairs of the items it updates;
     # an item whose tick is deferred reads and writes nothing (its potentials
-    # are brought up to date by a later update).
-    upd, dfr = br["item_ticks"]
-    units = upd * 128 / max(br["tick_launches"], 1)
-    bytes_launch = batched_bytes_per_sample_core_tick(net, vbytes) * units
+    # are brought up to date by a later update), an idle one reads no row.
+    act, idle, dfr = br["item_classes"]
+    nl = max(br["tick_launches"], 1)
+    units_act, units_idle = act * 128 / nl, idle * 128 / nl
+    units = units_act + units_idle
+    bytes_launch = (batched_bytes_per_sample_core_tick(net, vbytes, True) * units_act +
+                    batched_bytes_per_sample_core_tick(net, vbytes, False) * units_idle)
     achieved = bytes_launch / (kavg_ms * 1e-3) / 1e9
-    flops_launch = 2.0 * net.axons * net.neurons * units  # crossbar product of the updated items (an idle one issues 1/16 of it)
+    flops_launch = 2.0 * net.axons * net.neurons * units_act  # crossbar product of the active items (an idle one issues 1/16 of it)
     tflops = flops_launch / (kavg_ms * 1e-3) / 1e12
     roof = {"kernel": "batched_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(units),
             "peak_source": pk["source"] + " (hbm_gbs, of measured copy bandwidth)",
-            "avg_launch_us": kavg_ms * 1e3, "bytes_per_launch": bytes_launch,
-            "sample_core_units_per_launch": units, "deferred_item_tick_frac": dfr / max(upd + dfr, 1),
+            "timing": "one CUDA event pair recorded by each timed graph replay around its 24 tick launches",
+            "avg_launch_us": kavg_ms * 1e3, "tick_kernels_ms_per_step": br["kernel_ms"] / args.steps,
+            "bytes_per_launch": bytes_launch, "sample_core_units_per_launch": units,
+            "active_units_per_launch": units_act, "deferred_item_tick_frac": dfr / max(act + idle + dfr, 1),
             "tensor": {"achieved_tflops": tflops, "peak_tflops": pk["bf16_tflops_sustained"],
                        "frac": tflops / pk["bf16_tflops_sustained"], "kind": "tcgen05.mma kind::f16 (fp16, fp32 accumulate)"}}
     ekp = pr["kernel_ms"] / max(pr["kernel_launches"], 1)  # per tick
     pbytes = plain_bytes_per_core_tick(net) * net.n_cores
+    l2_gbs = measure_l2_copy(torch)
     plain = {"samples_per_sec": pr["samples"] * ws / (ms_p * 1e-3),
              "synaptic_events_per_sec": pr["events"] * ws / (ms_p * 1e-3),
              "ms_per_step": ms_p / max(1, min(args.steps, 2)), "samples_per_step": npl, "batch": 1,
              "kernel": {"name": "plain_window_kernel (persistent, grid barrier per tick)", "avg_tick_us": ekp * 1e3,
-                        "achieved_gbs": pbytes / (ekp * 1e-3) / 1e9,
-                        "frac_hbm": pbytes / (ekp * 1e-3) / 1e9 / pk["hbm_gbs"]}}
+                        "bound": "latency (state L2-resident at batch 1; grid barrier per tick)",
+                        "achieved_gbs": pbytes / (ekp * 1e-3) / 1e9, "l2_copy_gbs": l2_gbs,
+                        "frac_l2": pbytes / (ekp * 1e-3) / 1e9 / l2_gbs,
+                        "l2_peak_source": "measured in this run: torch copy of 2 x 16 MiB, L2-resident"}}
     e2e = e2e_batched(ranc, torch, net, x, nb)
 
-    cpu = None
+    cpu, ref_out = None, None
     if rank == 0 and not args.no_cpu_baseline:
         cr = oracle_rate(net, x[:256])
+        ref_out = cr["out"]
         cpu = {"value": cr["samples_per_s"], "unit": "samples/s", "cores": cr["threads"], "kind": "oracle",
                "sample": f"{cr['samples']} samples of the 512-core workload, 24 ticks each ({cr['seconds']:.1f} s)",
                "synaptic_events_per_sec": cr["events_per_s"]}
+    par = None
+    if rank == 0:
+        if ref_out is None:
+            ref_out = oracle_outputs(net, x, 16)
+        # the timed batched run, the plain run and the host-buffer run against the oracle, and
+        # the host-buffer run against the timed run on every sample
+        par = parity_check(ref_out, batched=br["counts"], plain=pr["counts"], e2e=e2e["counts"])
+        par["e2e_equals_batched_all_samples"] = bool(np.array_equal(e2e["counts"], br["counts"]))
+        par["equal"] = par["equal"] and par["e2e_equals_batched_all_samples"]
 
     samples_total = br["samples"] * ws
     line = {
@@ -577,15 +656,18 @@ def main():
                    "l2": "working set (1 GiB potentials + 1 GiB scheduler rows) larger than L2",
                    "parallelism": f"replicas x{ws} (samples sharded, no collective)"},
         "plain": plain, "batched_over_plain": (samples_total / (ms_b * 1e-3)) / plain["samples_per_sec"],
-        "roofline": roof, "cpu_baseline": cpu,
+        "roofline": roof, "cpu_baseline": cpu, "parity": par,
         "e2e": {"value": e2e["value"] * ws, "unit": "samples/s", "h2d_bytes_per_step": e2e["h2d"],
                 "d2h_bytes_per_step": e2e["d2h"]},
         "clocks": clk.summary(), "gpu_launches": int(br["launches"]),
+        "graph": {"captures": br["graph"][0], "replays": br["graph"][1]},
     }
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+    if par is not None and not par["equal"]:
+        sys.exit(1)  # a benchmark whose output differs from the oracle is not a result
 
 
 if __name__ == "__main__":

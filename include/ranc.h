@@ -172,6 +172,9 @@ int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, ui
  *     RANC_EINVAL with the limit in ranc_last_error.
  *   - The first call on a device looks up the scratch array's device address
  *     (once per device); make that first call before any stream capture.
+ *     The address is kept for the life of the process: after a reset of the
+ *     device's primary context (cudaDeviceReset) it is stale, so do not use
+ *     this entry point after one.
  *   - All calls in the process share the one array: calls that overlap on the
  *     GPU (other streams or threads) race.  Every call rewrites the part it
  *     uses, so no call depends on what an earlier call left there.
@@ -238,7 +241,13 @@ int ranc_load_state(ranc_sim *sim, const void *buf, size_t n);
  * ranc_read_kernel_timing returns their summed duration in milliseconds and
  * the number of ticks they advanced since timing was enabled (one per launch
  * for per-tick kernels; a persistent launch of ranc_run_samples advances
- * window x ceil(n_samples / batch) ticks); synchronous. */
+ * window x ceil(n_samples / batch) ticks); synchronous.  A window graph of
+ * ranc_run_samples (see ranc_graph_stats) recorded with timing on carries one
+ * event pair per group of samples, around that group's `window` tick kernels,
+ * so the replays themselves are timed; a replay folds the pairs of the
+ * previous one first (synchronising the stream), unless a
+ * ranc_read_kernel_timing call in between has done so.  Switching timing on
+ * or off makes the next such call record the graph again. */
 int ranc_set_kernel_timing(ranc_sim *sim, int32_t enable);
 int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
 
@@ -247,7 +256,7 @@ int ranc_read_kernel_timing(ranc_sim *sim, double *total_ms, int64_t *launches);
 int ranc_launch_count(const ranc_sim *sim, int64_t *launches);
 
 /* CUDA graphs of ranc_run_samples.  On the batched path with device buffers
- * (RANC_MEM_DEVICE, kernel timing off) the launch sequence of a call (per group
+ * (RANC_MEM_DEVICE) the launch sequence of a call (per group
  * of `batch` samples: reset, input transposition, `window` tick kernels, output
  * copy) depends only on its arguments, so the first call records it as a CUDA
  * graph and later calls with the same inputs, counts, n_samples, t_in and
@@ -274,6 +283,14 @@ int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays);
  * NULL; RANC_ESTATE on the plain path. */
 int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferred);
 
+/* The updated item-ticks of ranc_item_ticks split by what they read: *active
+ * receives those whose scheduler row or input lines could hold spikes (the row
+ * is read and cleared, the crossbar product runs), *idle those known to
+ * receive nothing (no row or input read; dV = 0), *deferred the deferred ones
+ * (active + idle = updated).  Same counting period, synchronisation and
+ * errors as ranc_item_ticks. */
+int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, int64_t *deferred);
+
 /* How the handle stores the membrane potentials in device memory.  The paper
  * makes the potential's bit width a configuration parameter (Sec. III and
  * Sec. V); the library picks, at ranc_create, the narrowest storage that holds
@@ -291,6 +308,13 @@ int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferred);
  * format.  *format receives one of the values above. */
 enum { RANC_POTENTIAL_INT32 = 0, RANC_POTENTIAL_INT16 = 1, RANC_POTENTIAL_FP16 = 2 };
 int ranc_potential_format(const ranc_sim *sim, int32_t *format);
+
+/* Number of device allocations (cudaMalloc calls that succeeded) the library
+ * has made in this process since it was loaded, over all handles and threads
+ * (the surrogate network of ranc_mlp.h included).  A diagnostic: callers and
+ * tests can check that a call allocates nothing.  Errors: RANC_EINVAL if
+ * count is NULL. */
+int ranc_device_allocations(int64_t *count);
 
 /* Free every device and host resource of the handle.  NULL is a no-op. */
 void ranc_destroy(ranc_sim *sim);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -195,10 +196,21 @@ cudaEvent_t next_event(ranc_sim *sim) {
     return sim->ev_pool[sim->ev_used++];
 }
 
-// Folds the recorded event pairs into timed_ms (synchronises the stream).
+// Folds the recorded event pairs into timed_ms (synchronises the stream):
+// the per-launch pairs and, after a timed window-graph launch, the pairs that
+// the graph records around each group's tick kernels.
 int fold_timing(ranc_sim *sim) {
-    if (sim->ev_used == 0) return RANC_OK;
+    if (sim->ev_used == 0 && !sim->win_pending) return RANC_OK;
     CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+    if (sim->win_pending) {
+        for (size_t i = 0; i + 1 < sim->win_events.size(); i += 2) {
+            float ms = 0.f;
+            CUDA_OR_FAIL(sim, cudaEventElapsedTime(&ms, sim->win_events[i], sim->win_events[i + 1]));
+            sim->timed_ms += ms;
+        }
+        sim->timed_launches += sim->win_key.window * (long long)sim->win_events.size() / 2;
+        sim->win_pending = 0;
+    }
     for (int i = 0; i + 1 < sim->ev_used; i += 2) {
         float ms = 0.f;
         CUDA_OR_FAIL(sim, cudaEventElapsedTime(&ms, sim->ev_pool[i], sim->ev_pool[i + 1]));
@@ -389,11 +401,23 @@ int read_counters4(ranc_sim *sim, unsigned long long *h4, int c0 = 0, int c1 = -
 
 }  // namespace
 
+namespace {
+std::atomic<long long> g_device_allocations{0};  // successful dev_alloc calls in this process
+}
+
 cudaError_t ranc::dev_alloc(void **p, size_t bytes) {
     *p = nullptr;
     if (g_alloc_budget == 0) return cudaErrorMemoryAllocation;
     if (g_alloc_budget > 0) g_alloc_budget--;
-    return cudaMalloc(p, bytes);
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_device_allocations.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+extern "C" int ranc_device_allocations(int64_t *count) {
+    if (!count) return RANC_EINVAL;
+    *count = (int64_t)g_device_allocations.load(std::memory_order_relaxed);
+    return RANC_OK;
 }
 
 void ranc::fault_alloc_arm_from_env() {
@@ -677,6 +701,7 @@ extern "C" int ranc_reset(ranc_sim *sim) {
         sim->ring_all_dirty = 1;  // a failed tick may have left any row written
     }
     sim->ev_used = 0;
+    sim->win_pending = 0;
     sim->in_override = nullptr;
     int rc = reset_state(sim, true);
     if (rc) return rc;
@@ -725,6 +750,7 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
     a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+    a.stall_test = sim->stall_test;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sim->timing) {
         if (sim->ev_used + 2 > 4096) {
@@ -761,17 +787,23 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
 }
 
 // Groups of B samples back to back: (reset, except before the first group),
-// inputs, `window` ticks, output counts.  Device buffers only.
-static int run_groups_device(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window, uint32_t *counts) {
+// inputs, `window` ticks, output counts.  Device buffers only.  `events`
+// (NULL, or two per group): recorded as external events right before the
+// group's first tick kernel and right after its last one, so that a recorded
+// graph carries its own timing of the tick kernels.
+static int run_groups_device(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window, uint32_t *counts,
+                             const cudaEvent_t *events = nullptr) {
     const size_t per = (size_t)t_in * sim->in_words;
-    for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
+    for (int s0 = 0, g = 0; s0 < n_samples; s0 += sim->B, ++g) {
         const int ns = std::min(sim->B, n_samples - s0);
         int rc = s0 > 0 ? reset_state(sim, false) : RANC_OK;
         if (rc) return rc;
         rc = load_inputs_dev(sim, t_in > 0 ? inputs + (size_t)s0 * per : nullptr, ns, t_in);
         if (rc) return rc;
+        if (events) CUDA_OR_FAIL(sim, cudaEventRecordWithFlags(events[2 * g], sim->stream, cudaEventRecordExternal));
         rc = step_ticks(sim, window);
         if (rc) return rc;
+        if (events) CUDA_OR_FAIL(sim, cudaEventRecordWithFlags(events[2 * g + 1], sim->stream, cudaEventRecordExternal));
         CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts + (size_t)s0 * sim->n_outputs, sim->out, (size_t)ns * sim->n_outputs * 4,
                                           cudaMemcpyDeviceToDevice, sim->stream));
     }
@@ -797,7 +829,13 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
     key.n_samples = n_samples;
     key.t_in = t_in;
     key.window = window;
-    if (sim->win_exec && key == sim->win_key) {
+    // With kernel timing on, the recording brackets each group's tick kernels
+    // with timing events (folded by the next synchronising timing call); the
+    // events of the previous launch are folded first, since a launch records
+    // over them.
+    const bool timed = sim->timing;
+    if (sim->win_pending && (rc = fold_timing(sim)) != RANC_OK) return rc;
+    if (sim->win_exec && key == sim->win_key && timed == sim->win_timed) {
         // Host bookkeeping of the recorded sequence, then one launch.
         sim->launches += sim->win_launches;
         sim->ticks_total += sim->win_ticks;
@@ -808,6 +846,7 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
         sim->pend_dirty = sim->win_pend_after;
         CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
         ++sim->graph_replays;
+        sim->win_pending = timed ? 1 : 0;
         return RANC_OK;
     }
     if (sim->win_exec) {
@@ -815,6 +854,16 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
         sim->win_exec = nullptr;
     }
     if (!sim->cap_stream) CUDA_OR_FAIL(sim, cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking));
+    const size_t n_ev = timed ? 2 * (size_t)((n_samples + sim->B - 1) / sim->B) : 0;
+    while (sim->win_events.size() < n_ev) {
+        cudaEvent_t ev;
+        CUDA_OR_FAIL(sim, cudaEventCreate(&ev));
+        sim->win_events.push_back(ev);
+    }
+    while (sim->win_events.size() > n_ev) {
+        cudaEventDestroy(sim->win_events.back());
+        sim->win_events.pop_back();
+    }
     // The recording reads no device state and the graph runs on the handle's
     // stream, after everything already queued there.
     const cudaStream_t stream = sim->stream;
@@ -826,7 +875,9 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
         sim->stream = stream;
         return fail(sim, RANC_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
     }
-    rc = run_groups_device(sim, inputs, n_samples, t_in, window, counts);
+    sim->timing = false;  // the per-launch events of step_ticks are replaced by the recorded ones
+    rc = run_groups_device(sim, inputs, n_samples, t_in, window, counts, timed ? sim->win_events.data() : nullptr);
+    sim->timing = timed;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(sim->stream, &graph);
     sim->stream = stream;
@@ -841,6 +892,7 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
         return fail(sim, RANC_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
     }
     sim->win_key = key;
+    sim->win_timed = timed;
     sim->win_launches = sim->launches - l0;
     sim->win_ticks = sim->ticks_total - t0;
     sim->win_tick_after = sim->tick;
@@ -848,6 +900,7 @@ static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_sample
     sim->win_pend_after = sim->pend_dirty;
     ++sim->graph_captures;
     CUDA_OR_FAIL(sim, cudaGraphLaunch(sim->win_exec, sim->stream));
+    sim->win_pending = timed ? 1 : 0;
     return RANC_OK;
 }
 
@@ -855,10 +908,23 @@ extern "C" int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferre
     CHECK_LIVE(sim);
     if (!updated || !deferred) return RANC_EINVAL;
     if (sim->path != RANC_PATH_BATCHED) return fail(sim, RANC_ESTATE, "item-ticks are counted on the batched path only");
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[3] = {0, 0, 0};
     cudaError_t e = batched_item_ticks(sim, h);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
     *updated = (int64_t)h[0];
+    *deferred = (int64_t)h[1];
+    return RANC_OK;
+}
+
+extern "C" int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, int64_t *deferred) {
+    CHECK_LIVE(sim);
+    if (!active || !idle || !deferred) return RANC_EINVAL;
+    if (sim->path != RANC_PATH_BATCHED) return fail(sim, RANC_ESTATE, "item-ticks are counted on the batched path only");
+    unsigned long long h[3] = {0, 0, 0};
+    cudaError_t e = batched_item_ticks(sim, h);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
+    *active = (int64_t)h[2];
+    *idle = (int64_t)(h[0] - h[2]);
     *deferred = (int64_t)h[1];
     return RANC_OK;
 }
@@ -882,7 +948,7 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
         int rc = run_windows_persistent(sim, inputs, n_samples, t_in, window, counts, mem);
         if (rc != RANC_ENOTSUP) return rc;  // otherwise fall through to per-tick launches
     }
-    if (sim->path == RANC_PATH_BATCHED && mem == RANC_MEM_DEVICE && !sim->timing) {
+    if (sim->path == RANC_PATH_BATCHED && mem == RANC_MEM_DEVICE) {
         int rc = run_samples_graph(sim, inputs, n_samples, t_in, window, counts);
         sim->in_override = nullptr;
         sim->n_valid = sim->B;
@@ -938,6 +1004,7 @@ static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in
     a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+    a.stall_test = sim->stall_test;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sim->timing) {
         if (sim->ev_used + 2 > 4096) {
@@ -1148,6 +1215,7 @@ extern "C" void ranc_destroy(ranc_sim *sim) {
     if (!sim) return;
     cudaStreamSynchronize(sim->stream);
     if (sim->win_exec) cudaGraphExecDestroy(sim->win_exec);
+    for (cudaEvent_t ev : sim->win_events) cudaEventDestroy(ev);
     if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
     free_all(sim);
     delete sim;

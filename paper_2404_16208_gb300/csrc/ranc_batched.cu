@@ -105,7 +105,9 @@ struct TickArgs {
     const uint8_t *pend_in;    // [items] idle ticks deferred before this tick
     uint8_t *pend_out;         // [items] idle ticks deferred after this tick
     int cost_active, cost_idle, cost_lazy, cost_wake, cost_first;  // relative costs for the split of the items over the CTAs
-    unsigned long long *item_ticks;  // [2]: items updated, items whose tick was deferred (accumulated)
+    unsigned long long *item_ticks;  // [3]: items updated, items whose tick was deferred, active items (accumulated)
+    int stall_test;            // failure-detection tests only: CTA 0 waits for a weight copy on a barrier
+                               // armed with a transaction count that no copy satisfies
 };
 
 constexpr int kPendMax = 250;  // deferred idle ticks of an item are applied before this many accumulate
@@ -320,9 +322,14 @@ __device__ __forceinline__ uint4 v_splat(int x) {
 
 // Deferred idle ticks of a lazy item: x <- max(x + pl, theta-) on every
 // potential of a unit (pl = ticks * leak <= 0; the result lies in
-// [theta-, x], so it is exact in every storage format).
+// [theta-, x], so it is exact in every storage format).  pl is a 64-bit
+// product: up to kPendMax ticks of a leak near the int32 limit do not fit
+// 32 bits, and x + pl is formed in 64 bits before the maximum.
 template <typename VT, int kVecs>
-__device__ __forceinline__ void defer_apply(uint4 (&q)[kVecs], int pl, int nth) {
+__device__ __forceinline__ void defer_apply(uint4 (&q)[kVecs], long long pl, int nth) {
+    // fp16 potentials and theta- lie within +-2048: any pl below -4096 gives
+    // theta-, so the clamped value is exact in fp32.
+    const float plf = (float)max(pl, -8192ll);
 #pragma unroll
     for (int e = 0; e < kVecs; ++e) {
         uint32_t w[4] = {q[e].x, q[e].y, q[e].z, q[e].w};
@@ -330,13 +337,14 @@ __device__ __forceinline__ void defer_apply(uint4 (&q)[kVecs], int pl, int nth) 
         for (int k = 0; k < 4; ++k) {
             if constexpr (std::is_same<VT, __half>::value) {
                 const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
-                const __half2 r = __floats2half2_rn(fmaxf(f.x + (float)pl, (float)nth), fmaxf(f.y + (float)pl, (float)nth));
+                const __half2 r = __floats2half2_rn(fmaxf(f.x + plf, (float)nth), fmaxf(f.y + plf, (float)nth));
                 w[k] = *reinterpret_cast<const uint32_t *>(&r);
             } else if constexpr (sizeof(VT) == 2) {
-                const int lo = max((int)(int16_t)(w[k] & 0xFFFFu) + pl, nth), hi = max(((int)w[k] >> 16) + pl, nth);
+                const int lo = (int)max((long long)(int16_t)(w[k] & 0xFFFFu) + pl, (long long)nth),
+                          hi = (int)max((long long)((int)w[k] >> 16) + pl, (long long)nth);
                 w[k] = ((uint32_t)lo & 0xFFFFu) | ((uint32_t)hi << 16);
             } else {
-                w[k] = (uint32_t)max((int)w[k] + pl, nth);
+                w[k] = (uint32_t)(int)max((long long)(int)w[k] + pl, (long long)nth);
             }
         }
         q[e] = make_uint4(w[0], w[1], w[2], w[3]);
@@ -503,10 +511,11 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     __syncthreads();
     const int i0 = cut_sh[0], i1 = cut_sh[1];
     const bool cls_cached = i1 - i0 <= kClsCap;
-    int fl = 0, n_up = 0, n_def = 0;
+    int fl = 0, n_up = 0, n_def = 0, n_act = 0;
     visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend) {
         if (!cls_cached && cls == 0) cls = 1;
         ++(cls != 0 ? n_up : n_def);
+        n_act += cls == 2;
         if (cls_cached) {
             const int k = it - i0;
             cls_sm[k] = (uint8_t)(cls | (pend ? 4 : 0));
@@ -522,12 +531,14 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     n_def = __reduce_add_sync(0xffffffffu, n_def);
     if (lane == 0 && n_up) atomicAdd(item_ticks, (unsigned long long)n_up);
     if (lane == 0 && n_def) atomicAdd(item_ticks + 1, (unsigned long long)n_def);
+    n_act = __reduce_add_sync(0xffffffffu, n_act);
+    if (lane == 0 && n_act) atomicAdd(item_ticks + 2, (unsigned long long)n_act);
 }
 
 template <typename VT, int kNegReset>
 __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_constant__ TickArgs a, const __grid_constant__ CUtensorMap wmap) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full, s_free, acc_full[2], acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_w, bar_drain, s_full, s_free, acc_full[2], acc_empty[2], bar_stall;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ long long wsum_sh[kThreads / 32];
@@ -559,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     if (tid == 0) {
         mbar_init(&bar_w, 1);
         mbar_init(&bar_drain, 1);
+        mbar_init(&bar_stall, 1);
         mbar_init(&s_full, kWorkers);
         mbar_init(&s_free, 1);
         for (int k = 0; k < 2; ++k) {
@@ -690,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     uint4 q[kVecs];
 #pragma unroll
                     for (int e = 0; e < kVecs; ++e) q[e] = vp[e * 32];
-                    defer_apply<VT>(q, pe * pr.x, pr.z);
+                    defer_apply<VT>(q, (long long)pe * pr.x, pr.z);
 #pragma unroll
                     for (int e = 0; e < kVecs; ++e) vp[e * 32] = q[e];
                 }
@@ -790,7 +802,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 const int buf = ne & 1;
                 if (ce != pc) {
                     const int4 pr = a.prm[(size_t)ce * N + n];  // leak, pos_thr, neg_thr, reset
-                    lam = pr.x - 0x4B400000;  // folds the bias of f32_bits_minus_bias
+                    // folds the bias of f32_bits_minus_bias; wrap-around (unsigned)
+                    // arithmetic: the sum below is exact whenever V + dV + leak fits int32
+                    lam = (int)((uint32_t)pr.x - 0x4B400000u);
                     pth = pr.y;
                     nth = pr.z;
                     rst = pr.w;
@@ -874,7 +888,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                             unpack16<VT>(vb[k % kPre], hf, v);
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                const int x = v[i] + f32_bits_minus_bias(d[i]) + lam;
+                                const int x = (int)((uint32_t)v[i] + (uint32_t)f32_bits_minus_bias(d[i]) + (uint32_t)lam);
                                 const bool fire = x >= pth;
                                 int y = kNegReset ? (x < nth ? rst : x) : max(x, nth);
                                 y = fire ? rst : y;
@@ -967,7 +981,17 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     for (int kb = 0; kb < KB; ++kb)
                         tma_load_3d(Wsm + (size_t)(hh * KB + kb) * kBlockBytes, &wmap, kb * 64, hh * 128, c, &bar_w);
                 w_pending = true;
-                if (!wait(&bar_w, nw & 1)) break;
+                uint64_t *wbar = &bar_w;
+                uint32_t wpar = nw & 1;
+                if (a.stall_test && blockIdx.x == 0 && nw == 0) {
+                    // Failure-detection test: the wait is moved to a barrier that
+                    // expects 16 bytes no copy delivers; it runs out, and the
+                    // weight copies just issued land (drain below) before exit.
+                    mbar_arrive_expect_tx(&bar_stall, 16u);
+                    wbar = &bar_stall;
+                    wpar = 0;
+                }
+                if (!wait(wbar, wpar)) break;
                 w_pending = false;
                 ++nw;
                 loaded = c;
@@ -1040,7 +1064,8 @@ __global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long ve
 }
 
 // Applies the idle ticks that lazy items deferred: V <- max(V + k * leak,
-// theta-) for k = pend[c * T + j] (exact: the result lies in [theta-, V]).
+// theta-) for k = pend[c * T + j] (exact: the result lies in [theta-, V];
+// formed in 64 bits, since k * leak may not fit 32).
 // Vector e of the interleaved layout as in batched_reset_v.
 template <typename VT>
 __global__ void batched_catch_up(VT *V, const uint8_t *pend, const int4 *prm, int C, int N, int T, long long vecs) {
@@ -1057,7 +1082,7 @@ __global__ void batched_catch_up(VT *V, const uint8_t *pend, const int4 *prm, in
         uint4 u = p[e];
         VT *x = reinterpret_cast<VT *>(&u);
 #pragma unroll
-        for (int i = 0; i < E; ++i) x[i] = v_from_int<VT>(max(v_to_int<VT>(x[i]) + k * pr.x, pr.z));
+        for (int i = 0; i < E; ++i) x[i] = v_from_int<VT>((int)max((long long)v_to_int<VT>(x[i]) + (long long)k * pr.x, (long long)pr.z));
         p[e] = u;
     }
 }
@@ -1163,7 +1188,7 @@ struct Batched {
     // Item activity: delivery stamps [16][spitch], deferred idle ticks
     // [2][spitch] (double-buffered by tick parity), per-core flags.
     uint8_t *stamp = nullptr, *pend = nullptr, *core_flags = nullptr;
-    unsigned long long *item_ticks = nullptr;  // [2] updated / deferred item-ticks since the last counter reset
+    unsigned long long *item_ticks = nullptr;  // [3] updated / deferred / active item-ticks since the last counter reset
     long long spitch = 0;
     bool any_lazy = false;
     // Relative cost of an active, idle and lazy item, of applying deferred
@@ -1295,7 +1320,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         dev_alloc((void **)&sim->cnt, (size_t)sim->T * C * 4 * 8) != cudaSuccess ||
         dev_alloc((void **)&bs->stamp, (size_t)kRows * bs->spitch) != cudaSuccess ||
         dev_alloc((void **)&bs->pend, (size_t)2 * bs->spitch) != cudaSuccess ||
-        dev_alloc((void **)&bs->core_flags, (size_t)C) != cudaSuccess || dev_alloc((void **)&bs->item_ticks, 16) != cudaSuccess) {
+        dev_alloc((void **)&bs->core_flags, (size_t)C) != cudaSuccess || dev_alloc((void **)&bs->item_ticks, 24) != cudaSuccess) {
         why = "device allocation of the batched state failed";
         return cudaErrorMemoryAllocation;
     }
@@ -1307,7 +1332,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         (e = cudaMemcpy(bs->core_flags, cfl.data(), (size_t)C, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(bs->stamp, 0, (size_t)kRows * bs->spitch)) != cudaSuccess ||
         (e = cudaMemset(bs->pend, 0, (size_t)2 * bs->spitch)) != cudaSuccess ||
-        (e = cudaMemset(bs->item_ticks, 0, 16)) != cudaSuccess) {
+        (e = cudaMemset(bs->item_ticks, 0, 24)) != cudaSuccess) {
         why = "copy of the batched network arrays";
         return e;
     }
@@ -1371,6 +1396,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.cost_active = bs->cost_active; a.cost_idle = bs->cost_idle; a.cost_lazy = bs->cost_lazy; a.cost_wake = bs->cost_wake;
     a.cost_first = bs->cost_first;
     a.item_ticks = bs->item_ticks;
+    a.stall_test = sim->stall_test;
     const int grid = std::min(bs->n_sm, a.items);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)
@@ -1452,13 +1478,14 @@ cudaError_t launch_batched_reset(ranc_sim *sim, bool counters) {
     }
     if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B_pad * sim->n_outputs * 4, sim->stream)) != cudaSuccess) return e;
     if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
-    if (counters && (e = cudaMemsetAsync(B_of(sim)->item_ticks, 0, 16, sim->stream)) != cudaSuccess) return e;
+    if (counters && (e = cudaMemsetAsync(B_of(sim)->item_ticks, 0, 24, sim->stream)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-// Updated and deferred item-ticks since the last counter reset (synchronises the stream).
-cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host2) {
-    cudaError_t e = cudaMemcpyAsync(host2, B_of(sim)->item_ticks, 16, cudaMemcpyDeviceToHost, sim->stream);
+// Updated, deferred and active item-ticks since the last counter reset
+// (synchronises the stream).
+cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host3) {
+    cudaError_t e = cudaMemcpyAsync(host3, B_of(sim)->item_ticks, 24, cudaMemcpyDeviceToHost, sim->stream);
     return e != cudaSuccess ? e : cudaStreamSynchronize(sim->stream);
 }
 

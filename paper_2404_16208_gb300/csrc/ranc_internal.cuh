@@ -56,7 +56,8 @@ struct PlainArgs {
     uint32_t *out;               // [B][n_out]
     unsigned long long *cnt;     // [B][C][4]    spikes, packets, outputs, synaptic events
     int *err;
-    int stall_test;              // test only: CTA (0, 0) waits on an mbarrier nothing arrives on
+    int stall_test;              // test only: CTA (0, 0) waits on an mbarrier nothing arrives on (per-tick
+                                 // kernel); CTA 0 skips its first grid-barrier arrival (persistent kernel)
     uint32_t *olog;              // NULL, or this tick's output-bus log: event (b, id) also adds 1 at
     long long olog_stride;       //   olog[b * olog_stride + id]
 };
@@ -168,6 +169,9 @@ struct ranc_sim {
                    t_in == o.t_in && window == o.window;
         }
     } win_key;
+    bool win_timed = false;              // the recording brackets each group's ticks with timing events
+    std::vector<cudaEvent_t> win_events; // [groups][2] timing events recorded by the graph (owned)
+    int win_pending = 0;                 // replays whose timing events are not folded yet (0 or 1)
     long long win_launches = 0;          // kernels in the recorded sequence
     unsigned long long win_ticks = 0;    // sample ticks it advances
     long long win_tick_after = 0;        // tick counter after it
@@ -200,7 +204,7 @@ cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cu
 cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
 cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
-cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host2);
+cudaError_t batched_item_ticks(ranc_sim *sim, unsigned long long *host3);  // updated, deferred, active
 cudaError_t launch_batched_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
 cudaError_t launch_batched_export(ranc_sim *sim, int b0, int nb, int *v_canon, uint32_t *spk_canon,
                                   uint32_t *ring_canon);

@@ -208,15 +208,18 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 // k * nblocks).  Thread 0 of each CTA arrives with one acquire-release atomic
 // (after the CTA barrier, so it publishes the whole CTA's writes) and, unless
 // it was the last to arrive, polls with acquire loads.  Returns false if the
-// wait gave up.
-__device__ bool grid_sync(unsigned *bar, unsigned nblocks, unsigned &gen, int *s_ok) {
+// wait gave up.  skip_arrival (failure-detection tests only): this CTA waits
+// without arriving, so the barrier cannot complete and every CTA's wait runs
+// out.
+__device__ bool grid_sync(unsigned *bar, unsigned nblocks, unsigned &gen, int *s_ok, bool skip_arrival = false) {
     __syncthreads();
     if (threadIdx.x == 0) {
         bool ok = true;
         const unsigned target = (gen + 1u) * nblocks;
-        unsigned v;
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
-        if (v + 1u != target && (int)(ld_acquire_u32(bar) - target) < 0) {
+        unsigned v = 0u;
+        if (!skip_arrival)
+            asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
+        if (skip_arrival || (v + 1u != target && (int)(ld_acquire_u32(bar) - target) < 0)) {
             const unsigned long long t0 = global_ns();
             while ((int)(ld_acquire_u32(bar) - target) < 0) {
                 if (global_ns() - t0 > kWaitLimitNs) {
@@ -306,7 +309,8 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
             for (int i = tid; i < a.n_out; i += blockDim.x) __stcg(a.out + (size_t)b * a.n_out + i, 0u);
         if (!w.stream)
             for (int i = tid; i < ipw; i += blockDim.x) inb[i] = valid ? __ldg(a.inputs + (size_t)smp * ipw + i) : 0u;
-        if (!grid_sync(w.bar, nblocks, gen, &s_ok)) break;
+        // Failure-detection test: CTA 0 does not arrive at the first barrier.
+        if (!grid_sync(w.bar, nblocks, gen, &s_ok, a.stall_test && blockIdx.x == 0 && win == 0)) break;
         bool stop = false;
         for (int t = 0; t < w.window; ++t) {
             const int r = t & (kRows - 1);

@@ -23,7 +23,8 @@ EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_read_core_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
-            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_item_ticks", "ranc_potential_format", "ranc_destroy",
+            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_item_ticks", "ranc_item_classes",
+            "ranc_potential_format", "ranc_device_allocations", "ranc_destroy",
             "ranc_last_error")
 RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
 
@@ -76,7 +77,9 @@ def load_library(path=LIB_PATH):
         "ranc_launch_count": ([vp, C.POINTER(i64)], C.c_int),
         "ranc_graph_stats": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_item_ticks": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "ranc_item_classes": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_potential_format": ([vp, C.POINTER(i32)], C.c_int),
+        "ranc_device_allocations": ([C.POINTER(i64)], C.c_int),
         "ranc_destroy": ([vp], None),
         "ranc_last_error": ([vp], C.c_char_p),
     }
@@ -250,6 +253,13 @@ def ranc_item_ticks(h):
     return u.value, d.value
 
 
+def ranc_item_classes(h):
+    """(active, idle, deferred) item-ticks of the batched tick kernel."""
+    a, i, d = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.ranc_item_classes(h, C.byref(a), C.byref(i), C.byref(d)), h)
+    return a.value, i.value, d.value
+
+
 def ranc_graph_stats(h):
     """(captures, replays) of ranc_run_samples' window graphs."""
     c, r = C.c_int64(), C.c_int64()
@@ -261,6 +271,13 @@ def ranc_potential_format(h):
     f = C.c_int32()
     _check(_lib.ranc_potential_format(h, C.byref(f)), h)
     return f.value
+
+
+def ranc_device_allocations():
+    """Device allocations the library has made in this process."""
+    n = C.c_int64()
+    _check(_lib.ranc_device_allocations(C.byref(n)), None)
+    return n.value
 
 
 def ranc_destroy(h):

@@ -37,3 +37,24 @@ def gpu_trace(sim, n_ticks):
         ss.append(unpack_spikes(s, sim.net.neurons))
         ds.append(d)
     return np.stack(vs, 1), np.stack(ss, 1), ds
+
+
+def idle_core_ticks(net, x, ref, n_ticks):
+    """[n_ticks, C] True where the core received no packet and no input in any
+    sample (computed from the oracle's spike trace)."""
+    C, A = net.n_cores, net.axons
+    act = np.zeros((n_ticks, C), bool)
+    pos = {(int(a), int(b)): k for k, (a, b) in enumerate(net.core_xy)}
+    d = net.dest
+    fired = ref["spike_trace"].any(0)  # [ticks, C, N]
+    for t in range(n_ticks):
+        for c, n in zip(*np.nonzero(fired[t])):
+            if d["kind"][c, n] == 1:
+                tt = t + int(d["delay"][c, n])
+                if tt < n_ticks:
+                    act[tt, pos[(int(net.core_xy[c, 0] + d["dx"][c, n]), int(net.core_xy[c, 1] + d["dy"][c, n]))]] = True
+    driven = np.zeros(C, bool)
+    driven[np.asarray(net.in_core)] = True
+    for t in range(min(x.shape[1], n_ticks)):
+        act[t] |= driven
+    return ~act

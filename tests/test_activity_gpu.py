@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import ranc_workloads as W
-from parity_util import digest, unpack_spikes
+from parity_util import digest, idle_core_ticks, unpack_spikes
 
 pytestmark = pytest.mark.gpu
 NPROC = os.cpu_count() or 1
@@ -38,27 +38,6 @@ def lazy_net(seed, w_lim=60, pthr=(1, 150), nthr=(-150, -1), hot_cores=()):
     for c in hot_cores:
         net.leak[c, ::17] = 1
     return net
-
-
-def idle_core_ticks(net, x, ref, n_ticks):
-    """[n_ticks, C] True where the core received no packet and no input in any
-    sample (computed from the oracle's spike trace)."""
-    C, A = net.n_cores, net.axons
-    act = np.zeros((n_ticks, C), bool)
-    pos = {(int(a), int(b)): k for k, (a, b) in enumerate(net.core_xy)}
-    d = net.dest
-    fired = ref["spike_trace"].any(0)  # [ticks, C, N]
-    for t in range(n_ticks):
-        for c, n in zip(*np.nonzero(fired[t])):
-            if d["kind"][c, n] == 1:
-                tt = t + int(d["delay"][c, n])
-                if tt < n_ticks:
-                    act[tt, pos[(int(net.core_xy[c, 0] + d["dx"][c, n]), int(net.core_xy[c, 1] + d["dy"][c, n]))]] = True
-    driven = np.zeros(C, bool)
-    driven[np.asarray(net.in_core)] = True
-    for t in range(min(x.shape[1], n_ticks)):
-        act[t] |= driven
-    return ~act
 
 
 def with_gap(x, g0, g1):
@@ -107,6 +86,38 @@ def test_idle_and_deferred_ticks_read_in_chunks(ranc, oracle_mod, fmt):
     # and this workload defers some
     upd, dfr = ranc.ranc_item_ticks(sim.h)
     assert upd + dfr == -(-B // 128) * net.n_cores * T and dfr > 0
+    sim.close()
+
+
+def test_deferred_ticks_with_a_leak_near_the_int32_limit(ranc, oracle_mod):
+    """int32 potentials, every other neuron of the first two layers leaking
+    -1e9 per tick down to theta- = -1e9: k deferred idle ticks apply k * leak,
+    which leaves 32 bits after three ticks; the result must still be
+    max(V + k * leak, theta-) as in the oracle's tick-by-tick int64
+    arithmetic, both when a state read applies the deferred ticks (layer 1 in
+    the input gap, layer 0 after the inputs) and when a core wakes up (layer 1
+    when the inputs resume)."""
+    w_lim, pthr, nthr = FORMATS[2]
+    net = lazy_net(47, w_lim=w_lim, pthr=pthr, nthr=nthr)
+    big = -10**9
+    for c in range(4):
+        net.leak[c, ::2] = big
+        net.neg_thr[c, ::2] = big
+    B, T = 140, 30
+    x = with_gap(W.rate_coded_inputs(19, B, 24, net.n_inputs, 0.35), 3, 20)
+    ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
+    assert (ref["v_trace"][:, :, :2, ::2] == big).any()  # the saturated neurons are there
+    sim = ranc.Sim(net, B, ranc.RANC_PATH_BATCHED)
+    assert sim.potential_format() == ranc.RANC_POTENTIAL_INT32
+    sim.load_inputs(x)
+    t = 0
+    for k in (2, 12, 8, 8):  # reads inside the input gap, after the wake-up, after the inputs
+        sim.step(k)
+        t += k
+        check_state(sim, ref, t - 1, "(leak -1e9)")
+    np.testing.assert_array_equal(sim.outputs(), ref["out"])
+    upd, dfr = ranc.ranc_item_ticks(sim.h)
+    assert dfr > 0
     sim.close()
 
 

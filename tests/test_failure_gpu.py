@@ -1,10 +1,15 @@
 """Failure detection without any GPU fault.
 
-* A test-only flag (RANC_TEST_STALL_WAIT) makes one CTA of the plain tick
-  kernel wait on an mbarrier that nothing arrives on.  The bounded wait must
-  give up after its limit, the next synchronising call must return
-  RANC_ETIMEOUT, later calls RANC_ESTATE, and ranc_reset must bring the handle
-  back to correct results.
+* A test-only flag (RANC_TEST_STALL_WAIT, read at ranc_create) makes one wait
+  of each kernel kind unable to complete: one CTA of the per-tick plain kernel
+  waits on an mbarrier that nothing arrives on; one CTA of the persistent
+  plain kernel does not arrive at the grid barrier, so every CTA's barrier
+  wait runs out; one CTA of the batched tensor-core kernel waits for its
+  weight copies on a barrier armed with a transaction count that no copy
+  satisfies (the copies it issued still land before it exits).  The bounded
+  waits must give up after their limit, the next synchronising call must
+  return RANC_ETIMEOUT, later calls RANC_ESTATE, and ranc_reset must bring the
+  handle back to correct results.
 * RANC_FAULT_ALLOC_AFTER=n makes the (n+1)-th device allocation of a create
   fail: every such create must return RANC_ENOMEM and free what it took.
 """
@@ -75,3 +80,48 @@ def test_allocation_failures_return_enomem_without_leaks(ranc, monkeypatch, path
     monkeypatch.delenv("RANC_FAULT_ALLOC_AFTER")
     assert succeeded_at is not None and succeeded_at >= 10
     assert abs(torch.cuda.mem_get_info()[0] - free0) < (8 << 20)
+
+
+def test_persistent_grid_barrier_wait_gives_up_and_reset_recovers(ranc, oracle_mod, monkeypatch):
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(6, 4, 8, 784, 0.15)
+    monkeypatch.setenv("RANC_TEST_STALL_WAIT", "1")
+    sim = ranc.Sim(net, 2, ranc.RANC_PATH_PLAIN)
+    monkeypatch.delenv("RANC_TEST_STALL_WAIT")
+    t0 = time.time()
+    with pytest.raises(ranc.RancError) as ei:  # the persistent window kernel (4 co-resident CTAs)
+        sim.run_samples(x, 9)
+    assert ei.value.code == ranc.RANC_ETIMEOUT
+    assert time.time() - t0 < 20
+    with pytest.raises(ranc.RancError) as ei:
+        sim.run_samples(x, 9)
+    assert ei.value.code == ranc.RANC_ESTATE
+    sim.reset()
+    ref = oracle_mod.run(net, x, 9)
+    np.testing.assert_array_equal(sim.run_samples(x, 9), ref["out"])
+    sim.close()
+
+
+def test_batched_weight_copy_wait_gives_up_and_reset_recovers(ranc, oracle_mod, monkeypatch):
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(7, 130, 8, 784, 0.15)
+    monkeypatch.setenv("RANC_TEST_STALL_WAIT", "1")
+    sim = ranc.Sim(net, 130, ranc.RANC_PATH_BATCHED)
+    monkeypatch.delenv("RANC_TEST_STALL_WAIT")
+    sim.load_inputs(x)
+    t0 = time.time()
+    sim.step(1)
+    with pytest.raises(ranc.RancError) as ei:
+        sim.outputs()
+    assert ei.value.code == ranc.RANC_ETIMEOUT
+    assert time.time() - t0 < 20
+    with pytest.raises(ranc.RancError) as ei:
+        sim.step(1)
+    assert ei.value.code == ranc.RANC_ESTATE
+    sim.reset()
+    sim.load_inputs(x)
+    sim.step(9)
+    ref = oracle_mod.run(net, x, 9)
+    np.testing.assert_array_equal(sim.outputs(), ref["out"])
+    np.testing.assert_array_equal(sim.state()[0], ref["v"])
+    sim.close()

@@ -157,6 +157,45 @@ def test_mnist512_full_batch_sampled(ranc, oracle_mod):
     sim.close()
 
 
+def test_mnist512_window_graph_as_benchmarked(ranc, oracle_mod):
+    """The benchmark's exact launch sequence: a 4096-sample handle, the inputs
+    and counts in device memory, ranc_run_samples recorded as a window graph
+    and replayed (deferred idle ticks included, no state read in between),
+    with and without the timing events the benchmark records.  64 samples
+    spread over all 32 tiles (two per tile, at varying positions) are compared
+    with the oracle: every output count, and every potential (and its digest)
+    after the window."""
+    import torch
+    net = W.mnist_512core()
+    B, t_in, window = 4096, 16, 24
+    x = W.rate_coded_inputs(net.meta["seed"], B, t_in, 784, 0.15)
+    picked = np.array([64 * k + (37 * k + 5) % 64 for k in range(64)])
+    assert len(set(picked // 128)) == 32
+    ref = oracle_mod.run(net, x[picked], window, n_threads=NPROC)
+    sim = ranc.Sim(net, B, ranc.RANC_PATH_BATCHED)
+    dx = torch.from_numpy(x.view(np.int32)).cuda()
+    dout = torch.zeros((B, net.n_outputs), dtype=torch.int32, device="cuda")
+    run = lambda: ranc.ranc_run_samples(sim.h, dx.data_ptr(), B, t_in, window, dout.data_ptr(), ranc.RANC_MEM_DEVICE)
+    for timed in (False, True):
+        ranc.ranc_set_kernel_timing(sim.h, timed)
+        for k in range(3):  # a recording, then replays
+            dout.zero_()
+            run()
+            out = dout.cpu().numpy().view(np.uint32)
+            np.testing.assert_array_equal(out[picked], ref["out"], err_msg=f"timed {timed}, call {k}")
+            v = np.stack([sim.sample_state(int(b), 1)[0][0] for b in picked])
+            np.testing.assert_array_equal(v, ref["v"], err_msg=f"timed {timed}, call {k}")
+            assert digest(v) == digest(ref["v"])
+        if timed:  # the replays timed their own tick kernels: 24 per call
+            ms, n = ranc.ranc_read_kernel_timing(sim.h)
+            assert n == 3 * window and ms > 0
+    assert ranc.ranc_graph_stats(sim.h) == (2, 4)  # one recording per timing setting
+    upd, dfr = ranc.ranc_item_ticks(sim.h)
+    act, idle, dfr2 = ranc.ranc_item_classes(sim.h)
+    assert act + idle == upd and dfr2 == dfr and dfr > 0  # the window defers idle ticks
+    sim.close()
+
+
 def test_batched_equals_plain_on_every_sample_of_a_large_batch(ranc, oracle_mod):
     """All 1000 samples (8 tiles, ragged) through both paths; the plain path
     is pinned to the oracle separately, and both are compared with the oracle
