@@ -40,16 +40,20 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_write.sum) per updated (sample, core) unit, from one ncu capture
 # of a tick in which every item of a 1024-sample case is updated; a launch's
 # traffic is that times the units it updates.  Valid only for the tick
-# kernel's source it was taken on: the sha256 of ranc_batched.cu up to its
-# helper-kernel section (see profiles/batched_tick_kernel_mnist512_1024samples.md).
+# kernel's source it was taken on (kernel_source_sha; see
+# profiles/batched_tick_kernel_mnist512_1024samples.md).
 PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "53b77895a4b86674", "bytes": 393.664000e6 + 236.722432e6,
                     "units": 1024 * 512}
 
 
 def kernel_source_sha():
+    """sha256 prefix of the tick kernel's source: ranc_batched.cu up to its
+    helper-kernel section, followed by the device helpers it includes."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2404_16208_gb300", "csrc", "ranc_batched.cu")).read()
-    return hashlib.sha256(src[:src.index("// Helper kernels: reset")].encode()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2404_16208_gb300", "csrc")
+    src = open(os.path.join(csrc, "ranc_batched.cu")).read()
+    src = src[:src.index("// Helper kernels: reset")] + open(os.path.join(csrc, "ranc_tc.cuh")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def profiled_traffic(units):

@@ -123,6 +123,51 @@ typedef struct ranc_sim ranc_sim;
  * error. */
 int ranc_create(const ranc_desc *desc, int32_t batch, int32_t path, void *cuda_stream, ranc_sim **out);
 
+/* Several networks of different core shapes simulated together in one
+ * batched handle: one tick launch updates every core of every network.  The
+ * paper motivates GPU simulation by the cost of exploring RANC's configuration
+ * space (core sizes, weight widths, axon types, thresholds, delays; Sec. I
+ * and Sec. V); a design sweep runs its configurations side by side here.
+ * descs[k] (k < n_networks <= 255) is a description as for ranc_create, each
+ * with axons a multiple of 64 in [64, 512], neurons a multiple of 128 in
+ * [128, 512] and the same neg_mode.  The networks share the batch and the
+ * input lines: the handle has max_k n_inputs lines and input line i drives,
+ * in every network that has a line i, what that network's fan-out says.
+ * Network k's cores and output-bus ids follow those of networks 0 .. k-1:
+ * global core = (cores of the networks before) + c, global output id = (ids
+ * of the networks before) + id; packets never leave their network.  Every
+ * entry point then works on the handle as on a batched one, with these
+ * shapes: ranc_read_outputs [batch][sum of n_outputs]; ranc_read_state and
+ * ranc_read_sample_state v [samples][P], spikes [samples][P / 32], where
+ * P = sum over k of n_cores_k * neurons_k (network k's block of cores at the
+ * offset of the networks before, each core's neurons in order);
+ * ranc_read_core_counters with global core ranges reads one network's
+ * activity.  ranc_run_stream, ranc_save_state, ranc_load_state and
+ * ranc_read_sample_state_noalloc return RANC_ESTATE on such a handle.
+ * The potentials use the narrowest storage exact for every network (see
+ * ranc_potential_format).  Errors: as ranc_create, with the failing
+ * network's index in ranc_last_error(NULL). */
+int ranc_create_multi(const ranc_desc *const *descs, int32_t n_networks, int32_t batch, void *cuda_stream,
+                      ranc_sim **out);
+
+/* Pipeline and split settings of a multi-network handle's tick kernel (the
+ * library's own tuning knobs; the paper sweeps CUDA block sizes by hand,
+ * Sec. IV).  A work item is one core on one tile of 128 samples; its crossbar
+ * product runs as MMAs over 128-neuron slices and 64-axon K-blocks, whose
+ * folded weights are copied into a ring of `weight_stages` 16 KB shared-memory
+ * stages ahead of the MMAs (2 .. max_weight_stages, which the largest axon
+ * count of the handle bounds).  The items of a tick are split over the CTAs by
+ * a cost prefix: an item that receives spikes costs cost_mma per (K-block,
+ * slice) plus cost_slice per slice, one that receives none cost_slice per
+ * slice.  Results do not depend on these settings, only the time does.
+ * ranc_set_multi_tuning synchronises the handle's stream, and the next
+ * ranc_run_samples call records its window graph again.  Errors:
+ * RANC_EINVAL for settings out of range, RANC_ESTATE on a handle made by
+ * ranc_create. */
+int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_mma, int32_t cost_slice);
+int ranc_get_multi_tuning(const ranc_sim *sim, int32_t *weight_stages, int32_t *max_weight_stages, int32_t *cost_mma,
+                          int32_t *cost_slice);
+
 /* Replace the input schedule with `bits` (host) [batch][n_ticks][ceil(n_inputs/32)]:
  * line i of input tick j is bit i%32 of word i/32 and is written into the
  * current scheduler row of the cores it drives at tick j counted from the last

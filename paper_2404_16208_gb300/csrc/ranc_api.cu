@@ -161,6 +161,7 @@ void free_all(ranc_sim *s) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     batched_teardown(s);
+    multi_teardown(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     s->ev_pool.clear();
 }
@@ -180,7 +181,9 @@ int sync_and_check(ranc_sim *sim) { return check_device_error(sim); }
 
 
 int reset_state(ranc_sim *sim, bool counters) {
-    cudaError_t e = sim->path == RANC_PATH_PLAIN ? launch_plain_reset(sim, counters) : launch_batched_reset(sim, counters);
+    cudaError_t e = sim->path == RANC_PATH_PLAIN ? launch_plain_reset(sim, counters)
+                    : sim->multi                ? launch_multi_reset(sim, counters)
+                                                : launch_batched_reset(sim, counters);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "reset: %s", cudaGetErrorString(e));
     sim->tick = 0;
     if (counters) sim->ticks_total = 0;
@@ -251,7 +254,7 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
         } else {
             BatchedArgs a{};
             a.tick = sim->tick;
-            e = launch_batched_tick(sim, a);
+            e = sim->multi ? launch_multi_tick(sim) : launch_batched_tick(sim, a);
         }
         sim->launches++;
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "tick kernel launch: %s", cudaGetErrorString(e));
@@ -292,7 +295,8 @@ int load_inputs_dev(ranc_sim *sim, const uint32_t *bits, int n_samples, int n_ti
                                           cudaMemcpyDeviceToDevice, sim->stream));
         return RANC_OK;
     }
-    cudaError_t e = launch_batched_inputs(sim, bits, n_samples, n_ticks);
+    cudaError_t e = sim->multi ? launch_multi_inputs(sim, bits, n_samples, n_ticks)
+                               : launch_batched_inputs(sim, bits, n_samples, n_ticks);
     if (e == cudaErrorMemoryAllocation) return fail(sim, RANC_ENOMEM, "batched input buffers");
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "batched input load: %s", cudaGetErrorString(e));
     return RANC_OK;
@@ -347,12 +351,15 @@ int canon_view(ranc_sim *sim, Canon &cv, bool need_ring) {
         cv.ring = sim->ring;
         return RANC_OK;
     }
+    if (sim->multi && need_ring)
+        return fail(sim, RANC_ESTATE, "checkpoints of a multi-network handle are not supported");
     cv.owned = true;
-    if (dmalloc(&cv.V, (size_t)sim->B * sim->C * sim->N) != cudaSuccess ||
-        dmalloc(&cv.spk, (size_t)sim->B * sim->C * (sim->N / 32)) != cudaSuccess ||
+    if (dmalloc(&cv.V, (size_t)sim->B * sim->nps) != cudaSuccess ||
+        dmalloc(&cv.spk, (size_t)sim->B * (sim->nps / 32)) != cudaSuccess ||
         (need_ring && dmalloc(&cv.ring, ring_words(sim)) != cudaSuccess))
         return fail(sim, RANC_ENOMEM, "temporary state buffers");
-    cudaError_t e = launch_batched_export(sim, 0, sim->B, cv.V, cv.spk, need_ring ? cv.ring : nullptr);
+    cudaError_t e = sim->multi ? launch_multi_export(sim, 0, sim->B, cv.V, cv.spk)
+                               : launch_batched_export(sim, 0, sim->B, cv.V, cv.spk, need_ring ? cv.ring : nullptr);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state export: %s", cudaGetErrorString(e));
     return RANC_OK;
 }
@@ -440,6 +447,7 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     if (!sim) return fail(nullptr, RANC_ENOMEM, "host allocation");
     const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types, AW = A / 32;
     sim->C = C; sim->A = A; sim->N = N; sim->K = K; sim->B = batch; sim->path = path; sim->neg_mode = d->neg_mode;
+    sim->nps = (long long)C * N;
     sim->grid_w = d->grid_w; sim->grid_h = d->grid_h; sim->n_inputs = d->n_inputs; sim->n_outputs = d->n_outputs;
     sim->in_words = (d->n_inputs + 31) / 32; sim->weight_bits = d->weight_bits;
     sim->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -561,6 +569,99 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
     return RANC_OK;
 }
 
+extern "C" int ranc_create_multi(const ranc_desc *const *descs, int32_t n_networks, int32_t batch, void *cuda_stream,
+                                 ranc_sim **out) {
+    if (!out) return fail(nullptr, RANC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!descs || n_networks < 1 || n_networks > 255) return fail(nullptr, RANC_EINVAL, "n_networks must be in [1, 255]");
+    std::string why;
+    int n_in = 0, n_out = 0, max_types = 1, max_a = 0, max_n = 0;
+    for (int s = 0; s < n_networks; s++) {
+        std::vector<int> core_at;
+        if (!validate(descs[s], batch, RANC_PATH_BATCHED, core_at, why))
+            return fail(nullptr, RANC_EINVAL, "network %d: %s", s, why.c_str());
+        const ranc_desc *d = descs[s];
+        if (!multi_shape_ok(d->axons, d->neurons))
+            return fail(nullptr, RANC_EINVAL,
+                        "network %d: a multi-network handle needs axons a multiple of 64 in [64, 512] and neurons a "
+                        "multiple of 128 in [128, 512] (got %d x %d)", s, d->axons, d->neurons);
+        if (d->neg_mode != descs[0]->neg_mode)
+            return fail(nullptr, RANC_EINVAL, "network %d: every network of a multi-network handle needs the same neg_mode", s);
+        if ((long long)n_out + d->n_outputs > (1 << 24)) return fail(nullptr, RANC_EINVAL, "too many output ids");
+        n_in = std::max(n_in, d->n_inputs);
+        n_out += d->n_outputs;
+        max_types = std::max(max_types, d->n_types);
+        max_a = std::max(max_a, d->axons);
+        max_n = std::max(max_n, d->neurons);
+    }
+    fault_alloc_arm_from_env();
+    ranc_sim *sim = new (std::nothrow) ranc_sim();
+    if (!sim) return fail(nullptr, RANC_ENOMEM, "host allocation");
+    sim->A = max_a; sim->N = max_n; sim->K = max_types; sim->B = batch; sim->path = RANC_PATH_BATCHED;
+    sim->neg_mode = descs[0]->neg_mode; sim->n_inputs = n_in; sim->n_outputs = n_out; sim->in_words = (n_in + 31) / 32;
+    sim->stream = static_cast<cudaStream_t>(cuda_stream);
+    sim->n_valid = batch;
+    {
+        const char *st = getenv("RANC_TEST_STALL_WAIT");
+        sim->stall_test = (st && *st && *st != '0') ? 1 : 0;
+    }
+    auto abort_create = [&](int code, const std::string &msg) {
+        g_alloc_budget = -1;
+        g_create_error = msg;
+        free_all(sim);
+        delete sim;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&sim->device);
+    if (e != cudaSuccess) return abort_create(RANC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dmalloc(&sim->err, 1) != cudaSuccess || dmalloc(&sim->digest, 8) != cudaSuccess)
+        return abort_create(RANC_ENOMEM, "device allocation failed");
+    if (cudaMemset(sim->err, 0, sizeof(int)) != cudaSuccess) return abort_create(RANC_ECUDA, "cudaMemset");
+    e = multi_setup(sim, descs, n_networks, why);
+    if (e == cudaErrorInvalidValue) return abort_create(RANC_EINVAL, why);
+    if (e == cudaErrorMemoryAllocation) return abort_create(RANC_ENOMEM, why);
+    if (e != cudaSuccess) return abort_create(RANC_ECUDA, why + ": " + cudaGetErrorString(e));
+    int rc = reset_state(sim, true);
+    if (rc == RANC_OK) rc = sync_and_check(sim);
+    if (rc != RANC_OK) {
+        std::string msg = sim->last_error;
+        return abort_create(rc, msg);
+    }
+    g_alloc_budget = -1;
+    *out = sim;
+    return RANC_OK;
+}
+
+extern "C" int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_mma, int32_t cost_slice) {
+    CHECK_LIVE(sim);
+    if (!sim->multi) return fail(sim, RANC_ESTATE, "the pipeline tuning belongs to multi-network handles");
+    int st = 0, mx = 0, cm = 0, cs = 0;
+    multi_get_tuning(sim, &st, &mx, &cm, &cs);
+    if (weight_stages < 2 || weight_stages > mx)
+        return fail(sim, RANC_EINVAL, "weight stages must be in [2, %d] for this handle (got %d)", mx, weight_stages);
+    if (cost_mma < 0 || cost_slice < 1 || cost_mma > 1024 || cost_slice > 1024)
+        return fail(sim, RANC_EINVAL, "split costs must satisfy 0 <= cost_mma <= 1024 and 1 <= cost_slice <= 1024");
+    CUDA_OR_FAIL(sim, multi_set_tuning(sim, weight_stages, cost_mma, cost_slice));
+    if (sim->win_exec) {  // a recorded window graph holds the old launch arguments
+        cudaGraphExecDestroy(sim->win_exec);
+        sim->win_exec = nullptr;
+    }
+    return RANC_OK;
+}
+
+extern "C" int ranc_get_multi_tuning(const ranc_sim *sim, int32_t *weight_stages, int32_t *max_weight_stages,
+                                     int32_t *cost_mma, int32_t *cost_slice) {
+    if (!sim || !weight_stages || !max_weight_stages || !cost_mma || !cost_slice) return RANC_EINVAL;
+    if (!sim->multi) return RANC_ESTATE;
+    int st = 0, mx = 0, cm = 0, cs = 0;
+    multi_get_tuning(sim, &st, &mx, &cm, &cs);
+    *weight_stages = st;
+    *max_weight_stages = mx;
+    *cost_mma = cm;
+    *cost_slice = cs;
+    return RANC_OK;
+}
+
 extern "C" int ranc_load_inputs(ranc_sim *sim, const uint32_t *bits, int32_t n_ticks) {
     CHECK_LIVE(sim);
     if (n_ticks < 0 || (n_ticks > 0 && !bits)) return fail(sim, RANC_EINVAL, "bad input arguments");
@@ -600,10 +701,10 @@ extern "C" int ranc_read_state(ranc_sim *sim, int32_t *v, uint32_t *spikes, uint
     Canon cv;
     int rc = canon_view(sim, cv, false);
     if (rc) return rc;
-    const size_t nv = (size_t)sim->B * sim->C * sim->N;
+    const size_t nv = (size_t)sim->B * sim->nps;
     if (v) CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, cv.V, nv * 4, cudaMemcpyDeviceToHost, sim->stream));
     if (spikes)
-        CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, cv.spk, (size_t)sim->B * sim->C * (sim->N / 32) * 4,
+        CUDA_OR_FAIL(sim, cudaMemcpyAsync(spikes, cv.spk, (size_t)sim->B * (sim->nps / 32) * 4,
                                           cudaMemcpyDeviceToHost, sim->stream));
     if (digest) {
         cudaError_t e = launch_digest(cv.V, (long long)nv, sim->digest, sim->stream);
@@ -618,7 +719,7 @@ extern "C" int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int
     CHECK_LIVE(sim);
     if (b0 < 0 || nb < 0 || (long long)b0 + nb > sim->B) return fail(sim, RANC_EINVAL, "sample range outside the batch");
     if (nb == 0) return RANC_OK;
-    const size_t per_v = (size_t)sim->C * sim->N, per_s = (size_t)sim->C * (sim->N / 32);
+    const size_t per_v = (size_t)sim->nps, per_s = (size_t)sim->nps / 32;
     if (sim->path == RANC_PATH_PLAIN) {
         if (v)
             CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, (int *)sim->V + (size_t)b0 * per_v, (size_t)nb * per_v * 4,
@@ -632,7 +733,8 @@ extern "C" int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int
     cv.owned = true;
     if (dmalloc(&cv.V, (size_t)nb * per_v) != cudaSuccess || dmalloc(&cv.spk, (size_t)nb * per_s) != cudaSuccess)
         return fail(sim, RANC_ENOMEM, "temporary state buffers");
-    cudaError_t e = launch_batched_export(sim, b0, nb, cv.V, cv.spk, nullptr);
+    cudaError_t e = sim->multi ? launch_multi_export(sim, b0, nb, cv.V, cv.spk)
+                               : launch_batched_export(sim, b0, nb, cv.V, cv.spk, nullptr);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "state export: %s", cudaGetErrorString(e));
     if (v) CUDA_OR_FAIL(sim, cudaMemcpyAsync(v, cv.V, (size_t)nb * per_v * 4, cudaMemcpyDeviceToHost, sim->stream));
     if (spikes)
@@ -643,6 +745,7 @@ extern "C" int ranc_read_sample_state(ranc_sim *sim, int32_t b0, int32_t nb, int
 extern "C" int ranc_read_sample_state_noalloc(ranc_sim *sim, int32_t b0, int32_t nb, int32_t *v, uint32_t *spikes) {
     CHECK_LIVE(sim);
     if (b0 < 0 || nb < 0 || (long long)b0 + nb > sim->B) return fail(sim, RANC_EINVAL, "sample range outside the batch");
+    if (sim->multi) return fail(sim, RANC_ESTATE, "the allocation-free read does not serve multi-network handles");
     const size_t per_v = (size_t)sim->C * sim->N, per_s = (size_t)sim->C * (sim->N / 32);
     if ((size_t)nb * (per_v + per_s) * 4 > kNoAllocScratchBytes)
         return fail(sim, RANC_EINVAL, "%d samples need %zu bytes of scratch; the allocation-free read holds at most %zu",
@@ -817,7 +920,8 @@ static int run_groups_device(ranc_sim *sim, const uint32_t *inputs, int n_sample
 // runs before the graph; everything after it is fixed by the arguments.
 static int run_samples_graph(ranc_sim *sim, const uint32_t *inputs, int n_samples, int t_in, int window, uint32_t *counts) {
     const void *inT = nullptr;
-    cudaError_t e = batched_reserve_inputs(sim, t_in, &inT);  // may allocate: never inside the recording
+    cudaError_t e = sim->multi ? multi_reserve_inputs(sim, t_in, &inT)  // may allocate: never inside the recording
+                               : batched_reserve_inputs(sim, t_in, &inT);
     if (e == cudaErrorMemoryAllocation) return fail(sim, RANC_ENOMEM, "batched input buffers");
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "batched input buffers: %s", cudaGetErrorString(e));
     int rc = reset_state(sim, false);
@@ -909,7 +1013,7 @@ extern "C" int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferre
     if (!updated || !deferred) return RANC_EINVAL;
     if (sim->path != RANC_PATH_BATCHED) return fail(sim, RANC_ESTATE, "item-ticks are counted on the batched path only");
     unsigned long long h[3] = {0, 0, 0};
-    cudaError_t e = batched_item_ticks(sim, h);
+    cudaError_t e = sim->multi ? multi_item_ticks(sim, h) : batched_item_ticks(sim, h);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
     *updated = (int64_t)h[0];
     *deferred = (int64_t)h[1];
@@ -921,7 +1025,7 @@ extern "C" int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, 
     if (!active || !idle || !deferred) return RANC_EINVAL;
     if (sim->path != RANC_PATH_BATCHED) return fail(sim, RANC_ESTATE, "item-ticks are counted on the batched path only");
     unsigned long long h[3] = {0, 0, 0};
-    cudaError_t e = batched_item_ticks(sim, h);
+    cudaError_t e = sim->multi ? multi_item_ticks(sim, h) : batched_item_ticks(sim, h);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
     *active = (int64_t)h[2];
     *idle = (int64_t)(h[0] - h[2]);
@@ -1037,6 +1141,7 @@ static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in
 extern "C" int ranc_run_stream(ranc_sim *sim, const uint32_t *inputs, int32_t n_in, int32_t n_ticks,
                                uint32_t *out_ticks, int32_t mem) {
     CHECK_LIVE(sim);
+    if (sim->multi) return fail(sim, RANC_ESTATE, "streaming runs of a multi-network handle are not supported");
     if (n_in < 0 || n_ticks < 0 || (n_in > 0 && !inputs) || (n_ticks > 0 && !out_ticks) ||
         (mem != RANC_MEM_HOST && mem != RANC_MEM_DEVICE))
         return fail(sim, RANC_EINVAL, "bad run_stream arguments");
@@ -1094,6 +1199,7 @@ extern "C" int ranc_run_stream(ranc_sim *sim, const uint32_t *inputs, int32_t n_
 
 extern "C" int ranc_save_state(ranc_sim *sim, void *buf, size_t *n) {
     CHECK_LIVE(sim);
+    if (sim->multi) return fail(sim, RANC_ESTATE, "checkpoints of a multi-network handle are not supported");
     if (!n) return fail(sim, RANC_EINVAL, "n is NULL");
     const size_t need = save_size(sim);
     if (!buf) {
@@ -1139,6 +1245,7 @@ __global__ void load_counters_kernel(unsigned long long *cnt, unsigned long long
 
 extern "C" int ranc_load_state(ranc_sim *sim, const void *buf, size_t n) {
     CHECK_LIVE(sim);
+    if (sim->multi) return fail(sim, RANC_ESTATE, "checkpoints of a multi-network handle are not supported");
     if (!buf || n < save_size(sim)) return fail(sim, RANC_EINVAL, "state buffer too small");
     SaveHeader h;
     memcpy(&h, buf, sizeof h);

@@ -122,6 +122,8 @@ struct ranc_sim {
     int *v0 = nullptr;
     void *wfold = nullptr;              // batched: [C][N][A] fp16 folded weights
     void *tmap = nullptr;               // batched: path-specific host state (tensor map, tables)
+    void *multi = nullptr;              // multi-network handle (ranc_create_multi): its host state
+    long long nps = 0;                  // neurons per sample (C * N, or the sum over a multi handle's networks)
 
     // state (device)
     void *V = nullptr;
@@ -213,4 +215,20 @@ cudaError_t launch_batched_import(ranc_sim *sim, const int *v_canon, const uint3
 cudaError_t batched_export_noalloc(ranc_sim *sim, int b0, int nb, int *v_host, uint32_t *spk_host);
 cudaError_t batched_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer);
 void batched_teardown(ranc_sim *sim);
+cudaError_t launch_transpose_inputs(const uint32_t *x, int n_samples, int ticks, int words, int T, uint32_t *inT,
+                                    cudaStream_t stream);
+// Implemented in ranc_multi.cu (several networks of different core shapes in
+// one batched handle, one tick launch for all of them)
+bool multi_shape_ok(int axons, int neurons);
+int multi_max_stages(int kbmax);
+cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std::string &why);
+cudaError_t launch_multi_tick(ranc_sim *sim);
+cudaError_t launch_multi_reset(ranc_sim *sim, bool counters);
+cudaError_t multi_item_ticks(ranc_sim *sim, unsigned long long *host3);  // updated, deferred, active
+cudaError_t multi_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer);
+cudaError_t launch_multi_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
+cudaError_t launch_multi_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk);
+void multi_get_tuning(const ranc_sim *sim, int *stages, int *max_stages, int *cost_mma, int *cost_slice);
+cudaError_t multi_set_tuning(ranc_sim *sim, int stages, int cost_mma, int cost_slice);
+void multi_teardown(ranc_sim *sim);
 }  // namespace ranc

@@ -19,7 +19,7 @@ RANC_OK, RANC_EINVAL, RANC_ENOMEM, RANC_ECUDA, RANC_ETIMEOUT, RANC_ESTATE = 0, -
 RANC_PATH_PLAIN, RANC_PATH_BATCHED = 0, 1
 RANC_MEM_HOST, RANC_MEM_DEVICE = 0, 1
 COUNTER_NAMES = ("spikes", "packets", "outputs", "synaptic_events", "ticks")
-EXPORTED = ("ranc_create", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
+EXPORTED = ("ranc_create", "ranc_create_multi", "ranc_set_multi_tuning", "ranc_get_multi_tuning", "ranc_load_inputs", "ranc_load_inputs_device", "ranc_step", "ranc_read_outputs",
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_read_core_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
@@ -56,6 +56,9 @@ def load_library(path=LIB_PATH):
     vp, i32, i64, u32p, u64p = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_void_p
     sig = {
         "ranc_create": ([C.POINTER(ranc_desc), i32, i32, vp, C.POINTER(vp)], C.c_int),
+        "ranc_create_multi": ([C.POINTER(C.POINTER(ranc_desc)), i32, i32, vp, C.POINTER(vp)], C.c_int),
+        "ranc_set_multi_tuning": ([vp, i32, i32, i32], C.c_int),
+        "ranc_get_multi_tuning": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
         "ranc_load_inputs": ([vp, u32p, i32], C.c_int),
         "ranc_load_inputs_device": ([vp, vp, i32], C.c_int),
         "ranc_step": ([vp, i32], C.c_int),
@@ -105,9 +108,9 @@ def _c(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
 
 
-def ranc_create(net, batch, path=RANC_PATH_PLAIN, stream=0):
-    """Create a simulator for ``net`` (any object with the fields of a RANC
-    network description) and return the opaque handle."""
+def _desc(net):
+    """A ranc_desc pointing into contiguous copies of ``net``'s arrays (which
+    the caller keeps alive while the description is used)."""
     keep = [_c(net.core_xy, np.int16), _c(net.crossbar, np.uint32), _c(net.axon_type, np.uint8),
             _c(net.weight, np.int16), _c(net.leak, np.int32), _c(net.pos_thr, np.int32),
             _c(net.neg_thr, np.int32), _c(net.reset, np.int32), _c(net.v0, np.int32),
@@ -117,9 +120,41 @@ def ranc_create(net, batch, path=RANC_PATH_PLAIN, stream=0):
     d = ranc_desc(net.grid_w, net.grid_h, net.n_cores, net.axons, net.neurons, net.n_types, net.weight_bits,
                   net.neg_mode, *[_p(a) for a in keep[:10]], net.n_inputs, net.n_outputs,
                   *[_p(a) for a in keep[10:]])
+    return d, keep
+
+
+def ranc_create(net, batch, path=RANC_PATH_PLAIN, stream=0):
+    """Create a simulator for ``net`` (any object with the fields of a RANC
+    network description) and return the opaque handle."""
+    d, keep = _desc(net)
     h = C.c_void_p()
     _check(_lib.ranc_create(C.byref(d), int(batch), int(path), C.c_void_p(int(stream)), C.byref(h)), None)
     return h
+
+
+def ranc_create_multi(nets, batch, stream=0):
+    """One batched handle simulating every network of ``nets`` (different
+    core shapes allowed) with one tick launch for all of them."""
+    descs, keep = [], []
+    for n in nets:
+        d, k = _desc(n)
+        descs.append(d)
+        keep.append(k)
+    arr = (C.POINTER(ranc_desc) * len(descs))(*[C.pointer(d) for d in descs])
+    h = C.c_void_p()
+    _check(_lib.ranc_create_multi(arr, len(descs), int(batch), C.c_void_p(int(stream)), C.byref(h)), None)
+    return h
+
+
+def ranc_set_multi_tuning(h, weight_stages, cost_mma, cost_slice):
+    _check(_lib.ranc_set_multi_tuning(h, int(weight_stages), int(cost_mma), int(cost_slice)), h)
+
+
+def ranc_get_multi_tuning(h):
+    """(weight_stages, max_weight_stages, cost_mma, cost_slice) of a multi-network handle."""
+    v = [C.c_int32() for _ in range(4)]
+    _check(_lib.ranc_get_multi_tuning(h, *[C.byref(x) for x in v]), h)
+    return tuple(x.value for x in v)
 
 
 def ranc_load_inputs(h, bits):
@@ -345,6 +380,82 @@ class Sim:
 
     def load(self, buf):
         ranc_load_state(self.h, buf)
+
+    def close(self):
+        if self.h is not None:
+            ranc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MultiSim:
+    """Owning wrapper around a multi-network handle (ranc_create_multi): the
+    networks share the batch and the input lines; results are returned per
+    network."""
+
+    def __init__(self, nets, batch, stream=0):
+        self.nets, self.batch = list(nets), int(batch)
+        self.h = ranc_create_multi(self.nets, batch, stream)
+        self.n_outputs = sum(n.n_outputs for n in self.nets)
+        self.ooff = np.concatenate([[0], np.cumsum([n.n_outputs for n in self.nets])]).astype(int)
+        self.coff = np.concatenate([[0], np.cumsum([n.n_cores for n in self.nets])]).astype(int)
+        self.poff = np.concatenate([[0], np.cumsum([n.n_cores * n.neurons for n in self.nets])]).astype(int)
+        self.n_inputs = max(n.n_inputs for n in self.nets)
+
+    def split_outputs(self, counts):
+        """[S, sum of n_outputs] -> list of [S, n_outputs_k]."""
+        return [counts[:, self.ooff[k]:self.ooff[k + 1]] for k in range(len(self.nets))]
+
+    def load_inputs(self, bits):
+        ranc_load_inputs(self.h, bits)
+
+    def step(self, n_ticks):
+        ranc_step(self.h, n_ticks)
+
+    def outputs(self):
+        return self.split_outputs(ranc_read_outputs(self.h, self.batch, self.n_outputs))
+
+    def run_samples(self, inputs, window):
+        """inputs uint32 [S, t_in, words] (words for the widest input count) ->
+        list of per-network counts [S, n_outputs_k]."""
+        inputs = _c(inputs, np.uint32)
+        counts = np.zeros((inputs.shape[0], self.n_outputs), np.uint32)
+        ranc_run_samples(self.h, inputs, inputs.shape[0], inputs.shape[1], window, counts)
+        return self.split_outputs(counts)
+
+    def sample_state(self, b0, nb):
+        """Per network: (v [nb, C_k, N_k], spikes [nb, C_k, N_k / 32])."""
+        P = int(self.poff[-1])
+        v = np.zeros((nb, P), np.int32)
+        s = np.zeros((nb, P // 32), np.uint32)
+        _check(_lib.ranc_read_sample_state(self.h, int(b0), int(nb), _p(v), _p(s)), self.h)
+        res = []
+        for k, n in enumerate(self.nets):
+            a, b = self.poff[k], self.poff[k + 1]
+            res.append((v[:, a:b].reshape(nb, n.n_cores, n.neurons),
+                        s[:, a // 32:b // 32].reshape(nb, n.n_cores, n.neurons // 32)))
+        return res
+
+    def counters(self):
+        """[n_networks, 4] spikes, packets, output events, synaptic events."""
+        return np.stack([ranc_read_core_counters(self.h, self.coff[k], self.coff[k + 1]) for k in range(len(self.nets))])
+
+    def reset(self):
+        ranc_reset(self.h)
+
+    def potential_format(self):
+        return ranc_potential_format(self.h)
+
+    def tuning(self):
+        return ranc_get_multi_tuning(self.h)
+
+    def set_tuning(self, weight_stages, cost_mma, cost_slice):
+        ranc_set_multi_tuning(self.h, weight_stages, cost_mma, cost_slice)
 
     def close(self):
         if self.h is not None:

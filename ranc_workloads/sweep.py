@@ -89,6 +89,12 @@ def sweep_net(seed, index, spec, n_inputs=1024, n_outputs=10, fanout=8, p_core=0
                        neg_mode=spec.neg_mode, meta=dict(spec=spec, index=index))
 
 
-def sweep(seed, n, **spec_kw):
-    """The n networks of a sweep (list of Net)."""
-    return [sweep_net(seed, i, sp) for i, sp in enumerate(sweep_specs(seed, n, **spec_kw))]
+def sweep(seed, n, workers=None, **spec_kw):
+    """The n networks of a sweep (list of Net), built on `workers` threads
+    (numpy releases the interpreter lock in its array loops)."""
+    import concurrent.futures as cf
+    import os
+    specs = sweep_specs(seed, n, **spec_kw)
+    workers = workers or min(8, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda a: sweep_net(seed, a[0], a[1]), enumerate(specs)))
