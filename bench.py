@@ -417,61 +417,129 @@ def bench_stream(ranc, torch, steps, warmup):
                              "cores": 1, "kind": "oracle", "sample": "the first 48 ticks of the stream"}}
 
 
-def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(16, 128), batch=256, t_in=16, window=32):
-    """A design sweep: n_cfg ragged random networks (core sizes {128, 256,
+SWEEP_SEED = 0x5EEDF1
+
+
+def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), batch=1024, t_in=16, window=32):
+    """The design sweep: n_cfg ragged random networks (core sizes {128, 256,
     512}^2, weight bits {4, 6, 9}, 2 or 4 axon types, density U[0.1, 0.5],
-    delays U{1..15}, cores U{core_range}, 1024 shared input lines), each run
-    on the same `batch` samples for `window` ticks.  A step simulates every
-    network once.  The autotuned plan (one combined launch per shape class
-    where that is faster) is timed against one handle per network."""
+    delays U{1..15}, cores U{core_range}, 1024 shared input lines), every one
+    on the same `batch` samples for `window` ticks, all in one multi-network
+    handle: one tick launch per tick for all of them.  The handle's pipeline
+    and split settings are autotuned on 128 probe samples first.  A step is
+    one window of every network (one graph replay, device buffers)."""
+    import concurrent.futures as cf
     import oracle
+    import ranc_workloads as W
     from ranc_workloads import sweep as SW
     from paper_2404_16208_gb300 import sweep as S
     t0 = time.perf_counter()
-    nets = SW.sweep(0x5EEDF1, n_cfg, core_range=core_range)
+    nets = SW.sweep(SWEEP_SEED, n_cfg, core_range=core_range)
     gen_s = time.perf_counter() - t0
-    import ranc_workloads as W
-    x = W.rate_coded_inputs(0x5EEDF1, batch, t_in, 1024, 0.15)
-    res = {}
-    for plan in ("auto", "separate"):
-        sw = S.Sweep(nets, batch, plan=plan, probe=64)
-        for _ in range(warmup):
-            outs = sw.run_samples(x, window)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            outs = sw.run_samples(x, window)
-        torch.cuda.synchronize()
-        sec = (time.perf_counter() - t0) / steps
-        res[plan] = dict(seconds=sec, plans=[[list(k), p, len(m)] for k, p, m in sw.plans()], tuning=sw.tuning,
-                         counts=[o.copy() for o in outs], counters=sw.counters().tolist())
-        sw.close()
-    same = all((a == b).all() for a, b in zip(res["auto"]["counts"], res["separate"]["counts"]))
-    events = sum(c[3] for c in res["separate"]["counters"]) / (warmup + steps)
-    # CPU oracle: one sample of the first 4 networks, extrapolated by A*N*cores*samples
-    oracle.build()
+    x = W.rate_coded_inputs(SWEEP_SEED, batch, t_in, 1024, 0.15)
     t0 = time.perf_counter()
-    work_done = 0
-    for n in nets[:4]:
-        oracle.run(n, x[:1, :, :(n.n_inputs + 31) // 32], window, n_threads=1)
-        work_done += n.n_cores * n.axons * n.neurons
+    sw = S.Sweep(nets, batch, plan="auto", probe=128)
+    outs_host = sw.run_samples(x, window)  # tuning, then one window through host buffers
+    tune_s = time.perf_counter() - t0
+    m = sw.multi_handle()
+    assert m is not None, "every network of the sweep joins one multi-network handle"
+    dx = torch.from_numpy(x.view(np.int32)).cuda()
+    dout = torch.zeros((batch, m.n_outputs), dtype=torch.int32, device="cuda")
+    run = lambda: ranc.ranc_run_samples(m.h, dx.data_ptr(), batch, t_in, window, dout.data_ptr(), ranc.RANC_MEM_DEVICE)
+    ranc.ranc_set_kernel_timing(m.h, True)
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    m.reset()
+    ranc.ranc_set_kernel_timing(m.h, True)
+    l0 = ranc.ranc_launch_count(m.h)
+    ms = 0.0
+    with Clocks(torch.cuda.current_device()) as clk:
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            ranc.ranc_read_kernel_timing(m.h)
+    launches = ranc.ranc_launch_count(m.h) - l0
+    kms, kn = ranc.ranc_read_kernel_timing(m.h)
+    ranc.ranc_set_kernel_timing(m.h, False)
+    counts = dout.cpu().numpy().view(np.uint32)
+    outs = m.split_outputs(counts)
+    cnt = m.counters()
+    ic = m.item_classes()  # [net, (active, idle)] item-ticks of the timed steps
+    fmt = m.potential_format()
+    tuning = m.tuning()
+    # Oracle: one seeded sample of every configuration (its output counts), on
+    # the host cores; this also times the oracle on that bounded sample.
+    picks = [(k, (k * 2654435761 + 12345) % batch) for k in range(n_cfg)]
+    oracle.build()
+
+    def one(kb):
+        k, b = kb
+        n = nets[k]
+        return oracle.run(n, x[b:b + 1, :, :(n.n_inputs + 31) // 32], window, n_threads=1)
+    thr = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(thr) as ex:
+        refs = list(ex.map(one, picks))
     cpu_s = time.perf_counter() - t0
-    work_all = sum(n.n_cores * n.axons * n.neurons for n in nets) * batch
+    par = {"compared": "output-bus counts of one seeded sample per configuration vs the CPU oracle",
+           "samples": n_cfg,
+           "timed_run": all(np.array_equal(outs[k][b], r["out"][0]) for (k, b), r in zip(picks, refs)),
+           "host_buffer_run_equals_timed_run": all(np.array_equal(a, b) for a, b in zip(outs_host, outs)),
+           "outputs_equal_output_counter": all(int(outs[k].sum()) * steps == int(cnt[k][2]) for k in range(n_cfg))}
+    par["equal"] = par["timed_run"] and par["host_buffer_run_equals_timed_run"] and par["outputs_equal_output_counter"]
+    # Roofline of the multi-network tick kernel: per updated (sample, core)
+    # unit the potentials read and written and the spike mask; per active
+    # unit the scheduler row read and cleared; per core that receives spikes
+    # in a tick its folded weights once (A * N fp16; the re-reads for its other
+    # sample tiles come from L2).
+    vb = 4 if fmt == ranc.RANC_POTENTIAL_INT32 else 2
+    T = -(-batch // 128)
+    nl = max(steps * window, 1)
+    bytes_launch = 0.0
+    units = 0.0
+    for k, n in enumerate(nets):
+        act, idle = ic[k]
+        bytes_launch += (act + idle) * 128 * (2 * n.neurons * vb + n.neurons // 8) + act * 128 * (2 * n.axons // 8)
+        bytes_launch += act / T * n.axons * n.neurons * 2
+        units += (act + idle) * 128
+    bytes_launch /= nl
+    units /= nl
+    kavg_ms = kms / max(kn, 1)
+    pk = peaks()
+    achieved = bytes_launch / (kavg_ms * 1e-3) / 1e9
+    events = float(cnt[:, 3].sum()) / steps
     cores = sum(n.n_cores for n in nets)
-    return {"metric": f"design sweep: seconds to simulate {n_cfg} ragged networks x {batch} samples x {window} ticks",
-            "value": res["auto"]["seconds"], "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": steps,
-            "warmup": warmup, "ms_per_step": 1e3 * res["auto"]["seconds"], "dtype": "per shape class (fp16/int32)",
-            "data": "synthetic", "config": {"workload": f"{n_cfg} networks, {cores} cores in all, sizes "
-                                                        "{128,256,512}^2, 1024 input lines",
-                                            "batch": batch, "window": window, "core_range": list(core_range)},
-            "config_samples_per_s": n_cfg * batch / res["auto"]["seconds"],
-            "synaptic_events_per_s": events / res["auto"]["seconds"],
-            "separate_handles_seconds": res["separate"]["seconds"],
-            "speedup_over_separate": res["separate"]["seconds"] / res["auto"]["seconds"],
-            "identical_results": bool(same), "plans": res["auto"]["plans"], "tuning": res["auto"]["tuning"],
-            "generation_seconds": gen_s,
-            "cpu_baseline": {"value": cpu_s * work_all / work_done, "unit": "s (extrapolated by A*N*cores*samples)",
-                             "cores": 1, "kind": "oracle", "sample": "one sample of the first 4 networks"}}
+    sec = ms / steps / 1e3
+    return {"metric": f"design sweep: configuration-samples/s ({n_cfg} ragged configurations x {batch} samples x "
+                      f"{window} ticks, one tick launch for all configurations)",
+            "value": n_cfg * batch / sec, "unit": "configuration-samples/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "dtype": POTENTIAL_DTYPE[fmt],
+            "data": "synthetic (seeded random networks, rate-coded 1024-line inputs, p=0.15)",
+            "config": {"workload": f"{n_cfg} networks, {cores} cores in all, core sizes {{128,256,512}}^2, "
+                                   f"cores U{{{core_range[0]}..{core_range[1]}}}, weight bits {{4,6,9}}, 2 or 4 types, "
+                                   "density U[0.1,0.5], delays U{1..15}",
+                       "batch": batch, "t_in": t_in, "window": window, "handle": "one multi-network handle"},
+            "synaptic_events_per_sec": events / sec, "gpu_launches": int(launches),
+            "launches_per_step": launches / steps, "tuning": {"chosen": {"weight_stages": tuning[0],
+                                                                           "max_weight_stages": tuning[1],
+                                                                           "cost_mma": tuning[2],
+                                                                           "cost_slice": tuning[3]},
+                                                                "candidates_seconds": next(iter(sw.tuning.values()))["seconds"]},
+            "roofline": {"kernel": "multi_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                         "peak_source": pk["source"] + " (hbm_gbs, of measured copy bandwidth)",
+                         "timing": "one CUDA event pair recorded by each timed graph replay around its tick launches",
+                         "avg_launch_us": kavg_ms * 1e3, "bytes_per_launch": bytes_launch,
+                         "sample_core_units_per_launch": units},
+            "parity": par, "clocks": clk.summary(), "generation_seconds": gen_s, "create_tune_first_run_seconds": tune_s,
+            "cpu_baseline": {"value": n_cfg / cpu_s, "unit": "configuration-samples/s", "cores": thr, "kind": "oracle",
+                             "sample": f"one sample of each of the {n_cfg} configurations, {window} ticks "
+                                       f"({cpu_s:.1f} s on {thr} threads, one configuration per thread)"}}
 
 
 def main():
@@ -538,7 +606,10 @@ def main():
         return
     if args.workload == "sweep":
         if rank == 0:
-            print(json.dumps(bench_sweep(ranc, torch, args.steps, args.warmup)))
+            line = bench_sweep(ranc, torch, args.steps, args.warmup)
+            print(json.dumps(line))
+            if not line["parity"]["equal"]:
+                sys.exit(1)
         return
     if args.workload == "dse":
         if rank == 0:

@@ -336,6 +336,12 @@ int ranc_item_ticks(ranc_sim *sim, int64_t *updated, int64_t *deferred);
  * errors as ranc_item_ticks. */
 int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, int64_t *deferred);
 
+/* ranc_item_classes for network k of a multi-network handle (ranc_create_multi;
+ * its ticks defer nothing): *active and *idle receive that network's
+ * item-ticks of each class.  Errors: RANC_EINVAL (NULL pointer, k out of
+ * range), RANC_ESTATE on other handles. */
+int ranc_network_item_classes(ranc_sim *sim, int32_t k, int64_t *active, int64_t *idle);
+
 /* How the handle stores the membrane potentials in device memory.  The paper
  * makes the potential's bit width a configuration parameter (Sec. III and
  * Sec. V); the library picks, at ranc_create, the narrowest storage that holds
@@ -353,6 +359,13 @@ int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, int64_t *de
  * format.  *format receives one of the values above. */
 enum { RANC_POTENTIAL_INT32 = 0, RANC_POTENTIAL_INT16 = 1, RANC_POTENTIAL_FP16 = 2 };
 int ranc_potential_format(const ranc_sim *sim, int32_t *format);
+/* The storage ranc_create would choose for `desc` on `path` (the same rule),
+ * without creating a handle or touching a device: a caller can size memory or
+ * group networks by storage before creating anything.  A multi-network handle
+ * takes the smallest of its networks' codes (int32 < int16 < fp16).  Errors:
+ * RANC_EINVAL for a NULL pointer, an unknown path or a description
+ * ranc_create would reject (reason in ranc_last_error(NULL)). */
+int ranc_desc_potential_format(const ranc_desc *desc, int32_t path, int32_t *format);
 
 /* Number of device allocations (cudaMalloc calls that succeeded) the library
  * has made in this process since it was loaded, over all handles and threads

@@ -1033,6 +1033,19 @@ extern "C" int ranc_item_classes(ranc_sim *sim, int64_t *active, int64_t *idle, 
     return RANC_OK;
 }
 
+extern "C" int ranc_network_item_classes(ranc_sim *sim, int32_t k, int64_t *active, int64_t *idle) {
+    CHECK_LIVE(sim);
+    if (!active || !idle) return RANC_EINVAL;
+    if (!sim->multi) return fail(sim, RANC_ESTATE, "per-network item-ticks belong to multi-network handles");
+    if (k < 0 || k >= multi_networks(sim)) return fail(sim, RANC_EINVAL, "network %d out of range", k);
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = multi_network_items(sim, k, h);
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "item-tick counters: %s", cudaGetErrorString(e));
+    *active = (int64_t)h[1];
+    *idle = (int64_t)(h[0] - h[1]);
+    return RANC_OK;
+}
+
 extern "C" int ranc_graph_stats(const ranc_sim *sim, int64_t *captures, int64_t *replays) {
     if (!sim || !captures || !replays) return RANC_EINVAL;
     *captures = sim->graph_captures;
@@ -1315,6 +1328,15 @@ extern "C" int ranc_potential_format(const ranc_sim *sim, int32_t *format) {
     static_assert(RANC_POTENTIAL_INT32 == kVInt32 && RANC_POTENTIAL_INT16 == kVInt16 && RANC_POTENTIAL_FP16 == kVHalf,
                   "storage codes");
     *format = sim->path == RANC_PATH_PLAIN ? RANC_POTENTIAL_INT32 : sim->vmode;
+    return RANC_OK;
+}
+
+extern "C" int ranc_desc_potential_format(const ranc_desc *desc, int32_t path, int32_t *format) {
+    if (!desc || !format || (path != RANC_PATH_PLAIN && path != RANC_PATH_BATCHED)) return RANC_EINVAL;
+    std::vector<int> core_at;
+    std::string why;
+    if (!validate(desc, 1, path, core_at, why)) return fail(nullptr, RANC_EINVAL, "%s", why.c_str());
+    *format = path == RANC_PATH_PLAIN ? RANC_POTENTIAL_INT32 : potential_format_of(desc);
     return RANC_OK;
 }
 

@@ -991,6 +991,27 @@ long long grid_for(long long n) { return std::max<long long>(1, std::min<long lo
 
 }  // namespace
 
+// Storage of the potentials on the batched paths.  After a tick a neuron
+// holds v0 (before its first tick), its reset value, theta-, or a value x
+// with theta- <= x < theta+, so every stored value lies in [lo, hi] below.
+// int16 holds that range exactly when it fits.  fp16 is exact for the update
+// (the tick kernels' fp16 branch) when [lo, hi] and [lo, hi] + leak lie
+// within +-2048 (every integer there is an fp16 value) and theta+, theta+ - 1,
+// theta-, theta- - 1 and the leak are representable.
+int potential_format_of(const ranc_desc *d) {
+    bool fits16 = true, fitsh = true;
+    for (size_t i = 0; i < (size_t)d->n_cores * d->neurons; i++) {
+        const long long pt = d->pos_thr[i], nt = d->neg_thr[i], r = d->reset[i], v0 = d->v0[i], lk = d->leak[i];
+        const long long hi = std::max({pt - 1, nt, r, v0});
+        const long long lo = std::min({nt, r, v0});
+        if (hi > 32767 || lo < -32768) fits16 = false;
+        if (lo < -2048 || hi > 2048 || lo + lk < -2048 || hi + lk > 2048 || lk < -2048 || lk > 2048 || pt < -2047 ||
+            pt > 2048 || nt < -2047 || nt > 2048)
+            fitsh = false;
+    }
+    return fitsh ? kVHalf : fits16 ? kVInt16 : kVInt32;
+}
+
 cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     const int C = d->n_cores, A = d->axons, N = d->neurons, K = d->n_types;
     if (!(N == 128 || N == 256) || A % 64 != 0 || A < 64 || A > 256) {
@@ -1022,24 +1043,7 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
     sim->T = (sim->B + kTileS - 1) / kTileS;
     sim->B_pad = sim->T * kTileS;
 
-    // Storage of the potentials.  After a tick a neuron holds v0 (before its
-    // first tick), its reset value, theta-, or a value x with theta- <= x <
-    // theta+, so every stored value lies in [lo, hi] below.  int16 holds that
-    // range exactly when it fits.  fp16 is exact for the update (the tick
-    // kernel's fp16 branch) when [lo, hi] and [lo, hi] + leak lie within
-    // +-2048 (every integer there is an fp16 value) and theta+, theta+ - 1,
-    // theta-, theta- - 1 and the leak are representable.
-    bool fits16 = true, fitsh = true;
-    for (size_t i = 0; i < (size_t)C * N; i++) {
-        const long long pt = d->pos_thr[i], nt = d->neg_thr[i], r = d->reset[i], v0 = d->v0[i], lk = d->leak[i];
-        const long long hi = std::max({pt - 1, nt, r, v0});
-        const long long lo = std::min({nt, r, v0});
-        if (hi > 32767 || lo < -32768) fits16 = false;
-        if (lo < -2048 || hi > 2048 || lo + lk < -2048 || hi + lk > 2048 || lk < -2048 || lk > 2048 || pt < -2047 ||
-            pt > 2048 || nt < -2047 || nt > 2048)
-            fitsh = false;
-    }
-    sim->vmode = fitsh ? kVHalf : fits16 ? kVInt16 : kVInt32;
+    sim->vmode = potential_format_of(d);
     // Largest delay of a core-to-core packet: bounds the scheduler rows that
     // can still hold deliveries when the handle is reset.
     sim->max_delay = 0;

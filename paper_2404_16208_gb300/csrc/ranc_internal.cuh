@@ -203,6 +203,7 @@ cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s);
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s);
 // Implemented in ranc_batched.cu
+int potential_format_of(const ranc_desc *d);  // kVHalf, kVInt16 or kVInt32 (storage rule of the batched paths)
 cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why);
 cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &a);
 cudaError_t launch_batched_reset(ranc_sim *sim, bool counters);
@@ -225,6 +226,8 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
 cudaError_t launch_multi_tick(ranc_sim *sim);
 cudaError_t launch_multi_reset(ranc_sim *sim, bool counters);
 cudaError_t multi_item_ticks(ranc_sim *sim, unsigned long long *host3);  // updated, deferred, active
+cudaError_t multi_network_items(ranc_sim *sim, int k, unsigned long long *host2);  // network k: updated, active
+int multi_networks(const ranc_sim *sim);
 cudaError_t multi_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer);
 cudaError_t launch_multi_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
 cudaError_t launch_multi_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk);

@@ -33,7 +33,11 @@
 //   warp 17    weight loader: the folded weights of every (slice, K-block) of
 //              the active items, 16 KB blocks stored pre-swizzled in global
 //              memory, copied by the TMA engine (cp.async.bulk) into a ring of
-//              weight stages ahead of the MMAs.
+//              weight stages ahead of the MMAs;
+//   warp 18    prefetcher: the potentials (one contiguous block per item) and
+//              the scheduler row of the items just ahead of the workers are
+//              brought into L2 by bulk prefetches (cp.async.bulk.prefetch.L2),
+//              so the epilogue's and the build's loads do not wait on HBM.
 // Every mbarrier wait is bounded (global timer); a timeout sets the device
 // error word and every role leaves its loop, drains the tensor core and the
 // copies in flight, and frees tensor memory before the CTA exits.
@@ -67,6 +71,8 @@ namespace {
 constexpr int kWorkersM = 16;                   // warps 0-15: operand build + epilogue
 constexpr int kIssuerWarpM = 16;                // tensor memory, MMA issue
 constexpr int kLoaderWarpM = 17;                // weight-block copies
+constexpr int kPrefetchWarpM = 18;              // L2 prefetch of the items ahead of the workers
+constexpr int kPrefetchAhead = 2;               // items prefetched ahead of the workers' epilogue
 constexpr int kThreadsM = (kWorkersM + 4) * 32;  // warps 16-19 form one warpgroup
 constexpr int kRegWorkerM = 104, kRegIssuerM = 48;
 static_assert(kWorkersM * 32 * kRegWorkerM + 4 * 32 * kRegIssuerM <= kThreadsM * 96, "register split exceeds the launch");
@@ -113,7 +119,8 @@ struct MultiArgs {
     uint32_t sclock;           // stamp clock of this tick
     int all_active;
     const uint8_t *core_flags; // [C] bit 0: some input line drives the core
-    unsigned long long *item_ticks;  // [3]: updated, deferred (always 0 here), active item-ticks
+    unsigned long long *item_ticks;  // [3 + 2 * n_seg]: updated, deferred (always 0 here), active item-ticks,
+                                     // then updated and active item-ticks of each network
     int kbmax;                 // largest A/64 of the handle: operand blocks kept in shared memory
     int stall_test;            // failure-detection tests only: CTA 0's issuer waits for its first weight
                                // block on a barrier armed with a transaction count no copy satisfies
@@ -177,12 +184,27 @@ __device__ __noinline__ void split_multi(const MultiArgs &a, const int *cost_sh,
     __syncthreads();
     const int i0 = cut_sh[0], i1 = cut_sh[1];
     int n_up = 0, n_act = 0;
+    int sg = -1, s_up = 0, s_act = 0;  // per-network counts of the current run of items
+    auto flush = [&]() {
+        if (sg >= 0 && s_up) {
+            atomicAdd(a.item_ticks + 3 + 2 * sg, (unsigned long long)s_up);
+            if (s_act) atomicAdd(a.item_ticks + 4 + 2 * sg, (unsigned long long)s_act);
+        }
+        s_up = s_act = 0;
+    };
     for (int it = max(t0, i0); it < min(t1, i1); ++it) {
-        const int cls = cls_of(it, it / T);
+        const int g = it / T, cls = cls_of(it, g);
         if (i1 - i0 <= kClsCapM) cls_sm[it - i0] = (uint8_t)cls;
         ++n_up;
         n_act += cls == 2;
+        if (core_seg[g] != sg) {
+            flush();
+            sg = core_seg[g];
+        }
+        ++s_up;
+        s_act += cls == 2;
     }
+    flush();
     n_up = __reduce_add_sync(0xffffffffu, n_up);
     n_act = __reduce_add_sync(0xffffffffu, n_act);
     if (lane == 0 && n_up) atomicAdd(a.item_ticks, (unsigned long long)n_up);
@@ -196,6 +218,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
         w_empty[kMaxStagesM], bar_drain, bar_stall;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
+    __shared__ volatile int cur_sh;  // item whose operand the workers build (prefetcher's position)
     __shared__ long long wsum_sh[kThreadsM / 32];
     __shared__ int cut_sh[2];
     __shared__ int cost_sh[2 * 256];
@@ -235,6 +258,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
         mbar_init(&bar_drain, 1);
         mbar_init(&bar_stall, 1);
         abort_sh = 0;
+        cur_sh = 0;
         cut_sh[0] = cut_sh[1] = 0;
         fence_mbar_init();
     }
@@ -277,6 +301,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
         int ns = 0;                       // accumulator slices consumed (ring position)
         bool stop = false;
         for (int k = 0; k <= n_items && !stop; ++k) {
+            if (warp == 0 && lane == 0) cur_sh = k;
             // ---- (1) build the operand of item k
             if (k < n_items && active_at(k)) {
                 const int it = i0 + k, g = it / T, j = it - g * T;
@@ -528,6 +553,27 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                 if (idx < 0) break;
                 mbar_wait_bounded(&w_full[idx % S], (idx / S) & 1);
             }
+        } else if (warp == kPrefetchWarpM && lane == 0) {
+            // ------------------------------------------------------------ prefetcher
+            // Item li is prefetched once the workers have reached li - ahead
+            // (polled with a bounded wait; no result depends on it).
+            constexpr size_t kv = sizeof(VT);
+            const unsigned long long t0 = global_ns();
+            for (int li = 0; li < n_items && !abort_sh; ++li) {
+                while (cur_sh + kPrefetchAhead < li && !abort_sh) {
+                    if (global_ns() - t0 > 4 * kWaitLimitNs) break;
+                    __nanosleep(200);
+                }
+                const int it = i0 + li, g = it / T, j = it - g * T;
+                const SegDev sd = a.seg[a.core_seg[g]];
+                const int c = g - sd.core0;
+                if (!a.v0_now)
+                    prefetch_l2(reinterpret_cast<const uint8_t *>(a.V) +
+                                    (sd.voff + v_index<VT>(j, c, 0, 0, 0, sd.C, sd.N)) * kv,
+                                (uint32_t)(128 * sd.N * kv));
+                if (active_at(li))
+                    prefetch_l2(a.ring + sd.roff + (((size_t)j * sd.C + c) * kRows + r0) * sd.A * 4, (uint32_t)sd.A * 16u);
+            }
         }
     }
     tc_fence_before();
@@ -585,7 +631,7 @@ struct Multi {
     uint32_t *outdeg = nullptr;
     uint4 *inT = nullptr;
     size_t inT_cap = 0;
-    unsigned long long *item_ticks = nullptr;  // [3]
+    unsigned long long *item_ticks = nullptr;  // [3 + 2 * n_seg]
     long long spitch = 0, ring_words = 0, v_elems = 0, spk_words = 0;
     std::vector<int> max_delay;       // per network: largest core-to-core delay
 };
@@ -637,8 +683,8 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
     const int T = sim->T;
 
     // Potential storage: the narrowest format that is exact for every network
-    // (the rule of the single-network batched path, over all neurons).
-    bool fits16 = true, fitsh = true;
+    // (kVInt32 < kVInt16 < kVHalf: the smallest code of the networks).
+    int vmode = kVHalf;
     int C_total = 0;
     long long P = 0, vsz_elems = 0, ring_w = 0, spk_w = 0, wblocks = 0, fptr_n = 0, aout_n = 0;
     m->seg.resize(n);
@@ -646,15 +692,9 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
     for (int s = 0; s < n; s++) {
         const ranc_desc *d = descs[s];
         const int C = d->n_cores, A = d->axons, N = d->neurons;
-        for (size_t i = 0; i < (size_t)C * N; i++) {
-            const long long pt = d->pos_thr[i], nt = d->neg_thr[i], r = d->reset[i], v0 = d->v0[i], lk = d->leak[i];
-            const long long hi = std::max({pt - 1, nt, r, v0}), lo = std::min({nt, r, v0});
-            if (hi > 32767 || lo < -32768) fits16 = false;
-            if (lo < -2048 || hi > 2048 || lo + lk < -2048 || hi + lk > 2048 || lk < -2048 || lk > 2048 || pt < -2047 ||
-                pt > 2048 || nt < -2047 || nt > 2048)
-                fitsh = false;
+        vmode = std::min(vmode, potential_format_of(d));
+        for (size_t i = 0; i < (size_t)C * N; i++)
             if (d->dest[i].kind == RANC_DEST_CORE) m->max_delay[s] = std::max<int>(m->max_delay[s], d->dest[i].delay);
-        }
         SegDev &sd = m->seg[s];
         sd.C = C; sd.A = A; sd.N = N; sd.NH = N / 128; sd.KB = A / 64; sd.core0 = C_total;
         sd.voff = vsz_elems; sd.roff = ring_w; sd.soff = spk_w; sd.poff = P; sd.woff = wblocks; sd.foff = fptr_n;
@@ -673,7 +713,7 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
         aout_n += (long long)C * A;
         m->kbmax = std::max(m->kbmax, sd.KB);
     }
-    sim->vmode = fitsh ? kVHalf : fits16 ? kVInt16 : kVInt32;
+    sim->vmode = vmode;
     sim->max_delay = 0;
     for (int s = 0; s < n; s++) sim->max_delay = std::max(sim->max_delay, m->max_delay[s]);
     m->stages = std::min(4, multi_max_stages(m->kbmax));
@@ -766,7 +806,7 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
         dev_alloc((void **)&sim->out, (size_t)sim->B_pad * sim->n_outputs * 4) != cudaSuccess ||
         dev_alloc((void **)&sim->cnt, (size_t)T * C_total * 4 * 8) != cudaSuccess ||
         dev_alloc((void **)&m->stamp, (size_t)kRows * m->spitch) != cudaSuccess ||
-        dev_alloc((void **)&m->item_ticks, 24) != cudaSuccess) {
+        dev_alloc((void **)&m->item_ticks, (3 + 2 * (size_t)n) * 8) != cudaSuccess) {
         why = "device allocation of the multi-network state failed";
         return cudaErrorMemoryAllocation;
     }
@@ -782,7 +822,7 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
         (e = cudaMemcpy(sim->dst, dst.data(), dst.size() * sizeof(uint2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sim->v0, v0.data(), v0.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(m->stamp, 0, (size_t)kRows * m->spitch)) != cudaSuccess ||
-        (e = cudaMemset(m->item_ticks, 0, 24)) != cudaSuccess) {
+        (e = cudaMemset(m->item_ticks, 0, (3 + 2 * (size_t)n) * 8)) != cudaSuccess) {
         why = "copy of the multi-network arrays";
         return e;
     }
@@ -851,7 +891,8 @@ cudaError_t launch_multi_reset(ranc_sim *sim, bool counters) {
     }
     if ((e = cudaMemsetAsync(sim->out, 0, (size_t)sim->B_pad * sim->n_outputs * 4, sim->stream)) != cudaSuccess) return e;
     if (counters && (e = cudaMemsetAsync(sim->cnt, 0, sim->cnt_len * 8, sim->stream)) != cudaSuccess) return e;
-    if (counters && (e = cudaMemsetAsync(m->item_ticks, 0, 24, sim->stream)) != cudaSuccess) return e;
+    if (counters && (e = cudaMemsetAsync(m->item_ticks, 0, (3 + 2 * (size_t)m->n_seg) * 8, sim->stream)) != cudaSuccess)
+        return e;
     return cudaSuccess;
 }
 
@@ -859,6 +900,13 @@ cudaError_t multi_item_ticks(ranc_sim *sim, unsigned long long *host3) {
     cudaError_t e = cudaMemcpyAsync(host3, M_of(sim)->item_ticks, 24, cudaMemcpyDeviceToHost, sim->stream);
     return e != cudaSuccess ? e : cudaStreamSynchronize(sim->stream);
 }
+
+cudaError_t multi_network_items(ranc_sim *sim, int k, unsigned long long *host2) {
+    cudaError_t e = cudaMemcpyAsync(host2, M_of(sim)->item_ticks + 3 + 2 * (size_t)k, 16, cudaMemcpyDeviceToHost, sim->stream);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(sim->stream);
+}
+
+int multi_networks(const ranc_sim *sim) { return static_cast<const Multi *>(sim->multi)->n_seg; }
 
 cudaError_t multi_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer) {
     Multi *m = M_of(sim);

@@ -23,8 +23,8 @@ EXPORTED = ("ranc_create", "ranc_create_multi", "ranc_set_multi_tuning", "ranc_g
             "ranc_read_outputs_device", "ranc_read_state", "ranc_read_sample_state", "ranc_read_sample_state_noalloc",
             "ranc_read_counters", "ranc_read_core_counters", "ranc_get_tick", "ranc_reset",
             "ranc_run_samples", "ranc_run_stream", "ranc_save_state", "ranc_load_state", "ranc_set_kernel_timing",
-            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_item_ticks", "ranc_item_classes",
-            "ranc_potential_format", "ranc_device_allocations", "ranc_destroy",
+            "ranc_read_kernel_timing", "ranc_launch_count", "ranc_graph_stats", "ranc_item_ticks", "ranc_item_classes", "ranc_network_item_classes",
+            "ranc_potential_format", "ranc_desc_potential_format", "ranc_device_allocations", "ranc_destroy",
             "ranc_last_error")
 RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
 
@@ -81,7 +81,9 @@ def load_library(path=LIB_PATH):
         "ranc_graph_stats": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_item_ticks": ([vp, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_item_classes": ([vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "ranc_network_item_classes": ([vp, i32, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "ranc_potential_format": ([vp, C.POINTER(i32)], C.c_int),
+        "ranc_desc_potential_format": ([C.POINTER(ranc_desc), i32, C.POINTER(i32)], C.c_int),
         "ranc_device_allocations": ([C.POINTER(i64)], C.c_int),
         "ranc_destroy": ([vp], None),
         "ranc_last_error": ([vp], C.c_char_p),
@@ -295,6 +297,13 @@ def ranc_item_classes(h):
     return a.value, i.value, d.value
 
 
+def ranc_network_item_classes(h, k):
+    """(active, idle) item-ticks of network k of a multi-network handle."""
+    a, i = C.c_int64(), C.c_int64()
+    _check(_lib.ranc_network_item_classes(h, int(k), C.byref(a), C.byref(i)), h)
+    return a.value, i.value
+
+
 def ranc_graph_stats(h):
     """(captures, replays) of ranc_run_samples' window graphs."""
     c, r = C.c_int64(), C.c_int64()
@@ -305,6 +314,15 @@ def ranc_graph_stats(h):
 def ranc_potential_format(h):
     f = C.c_int32()
     _check(_lib.ranc_potential_format(h, C.byref(f)), h)
+    return f.value
+
+
+def ranc_desc_potential_format(net, path=RANC_PATH_BATCHED):
+    """The potential storage ranc_create would choose for ``net`` on ``path``
+    (no handle, no device work)."""
+    d, keep = _desc(net)
+    f = C.c_int32()
+    _check(_lib.ranc_desc_potential_format(C.byref(d), int(path), C.byref(f)), None)
     return f.value
 
 
@@ -453,6 +471,10 @@ class MultiSim:
 
     def tuning(self):
         return ranc_get_multi_tuning(self.h)
+
+    def item_classes(self):
+        """[n_networks, 2] active and idle item-ticks of each network."""
+        return np.array([ranc_network_item_classes(self.h, k) for k in range(len(self.nets))], np.int64)
 
     def set_tuning(self, weight_stages, cost_mma, cost_slice):
         ranc_set_multi_tuning(self.h, weight_stages, cost_mma, cost_slice)

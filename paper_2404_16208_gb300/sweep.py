@@ -1,10 +1,21 @@
 """Design sweeps: many independent RANC networks simulated together.
 
 Exploring RANC's configuration space means simulating many variants of a
-network (Sec. I, Sec. V).  Small or medium networks do not fill a GB300 one at
-a time, so a sweep is run here with as few launches per tick as possible:
-networks of one *shape class* are merged into one combined network, and every
-tick of the whole class is one tick launch of the library's kernels.
+network (Sec. I, Sec. V).  A sweep is run here with as few launches per tick
+as possible.  Plans:
+
+* ``multi`` (the default through ``auto``): every network whose core shape the
+  multi-network path takes (axons a multiple of 64 up to 512, neurons a
+  multiple of 128 up to 512) joins one multi-network handle
+  (``ranc_create_multi``) per negative-threshold mode, so one tick launch
+  updates every core of every such network; the rest fall back to ``combined``.
+  ``auto`` also tunes that handle: it times every weight-stage depth and a few
+  split cost settings (``ranc_set_multi_tuning``) on the first ``probe``
+  samples and keeps the fastest (cached by the sweep's signature when
+  ``cache`` names a JSON file).
+* ``combined``: networks of one *shape class* are merged into one combined
+  network (below), one tick launch per class.
+* ``separate``: one handle per network.
 
 Combined network of a class (exact: each member's results are those of
 simulating it alone):
@@ -25,9 +36,7 @@ simulating it alone):
 A class is (path, axons, neurons, negative-threshold mode, potential format):
 cores with at most 256 axons and neurons go to the batched (tensor-core) path,
 padded to 128 or 256 neurons and a multiple of 64 axons; larger cores go to the
-plain path with their own sizes.  :class:`Sweep` picks, per class, between one
-combined handle and one handle per member by timing both on the first samples
-(``plan="auto"``), and reads each member's counters through
+plain path with their own sizes.  Each network's counters are read through
 ``ranc_read_core_counters``.
 """
 
@@ -45,18 +54,13 @@ FORMAT_NAMES = {ranc.RANC_POTENTIAL_INT32: "int32", ranc.RANC_POTENTIAL_INT16: "
 
 def potential_format(net):
     """The storage the library chooses for this network's potentials on the
-    batched path (the rule of ranc_potential_format)."""
-    pt, nt = net.pos_thr.astype(np.int64), net.neg_thr.astype(np.int64)
-    r, v0, lk = net.reset.astype(np.int64), net.v0.astype(np.int64), net.leak.astype(np.int64)
-    hi = np.maximum.reduce([pt - 1, nt, r, v0])
-    lo = np.minimum.reduce([nt, r, v0])
-    half = ((lo >= -2048) & (hi <= 2048) & (lo + lk >= -2048) & (hi + lk <= 2048) & (np.abs(lk) <= 2048) &
-            (pt >= -2047) & (pt <= 2048) & (nt >= -2047) & (nt <= 2048))
-    if half.all():
-        return ranc.RANC_POTENTIAL_FP16
-    if (hi <= 32767).all() and (lo >= -32768).all():
-        return ranc.RANC_POTENTIAL_INT16
-    return ranc.RANC_POTENTIAL_INT32
+    batched path (asked from the library: ranc_desc_potential_format)."""
+    return ranc.ranc_desc_potential_format(net, ranc.RANC_PATH_BATCHED)
+
+
+def multi_ok(net):
+    """Whether the multi-network path takes this network's core shape."""
+    return net.axons % 64 == 0 and 64 <= net.axons <= 512 and net.neurons % 128 == 0 and 128 <= net.neurons <= 512
 
 
 def shape_class(net):
@@ -158,28 +162,65 @@ class _Group:
         self.sims = []
 
 
+class _MultiGroup:
+    """Members simulated by one multi-network handle (one tick launch)."""
+
+    def __init__(self, key, members, nets, batch, tuning=None):
+        self.key, self.members, self.plan = key, members, "multi"
+        self.sim = ranc.MultiSim([nets[i] for i in members], batch)
+        self.sims = [self.sim]
+        if tuning is not None:
+            self.sim.set_tuning(*tuning)
+
+    def run(self, nets, x, window):
+        outs = self.sim.run_samples(x[..., :(self.sim.n_inputs + 31) // 32], window)
+        return dict(zip(self.members, outs))
+
+    def counters(self):
+        return dict(zip(self.members, self.sim.counters()))
+
+    def reset(self):
+        self.sim.reset()
+
+    def close(self):
+        self.sim.close()
+        self.sims = []
+
+
+# Split cost settings (cost_mma, cost_slice) the tuner tries beside every weight-stage depth.
+COST_CANDIDATES = ((1, 4), (1, 2), (2, 4), (1, 8))
+
+
 class Sweep:
     """Many networks, one call: ``run_samples(inputs, window)`` returns each
     network's output counts; ``counters()`` each network's spikes, packets,
     output events and synaptic events.
 
-    ``plan``: "combined" (one handle per class), "separate" (one handle per
-    network) or "auto" (per class, the faster of the two on the first
-    ``probe`` samples of the first run; the choice and both times are kept in
-    ``tuning`` and, when ``cache`` names a JSON file, reused for the same
-    class signature)."""
+    ``plan``: "auto" (the multi-network plan with its pipeline and split
+    settings tuned on the first ``probe`` samples of the first run; the
+    candidates' times and the choice are kept in ``tuning`` and, when
+    ``cache`` names a JSON file, reused for the same sweep signature),
+    "multi" (the same with the library's default settings), "combined" (one
+    handle per shape class) or "separate" (one handle per network)."""
 
     def __init__(self, nets, batch, plan="auto", probe=128, cache=None):
         self.nets, self.batch, self.plan, self.probe, self.cache = list(nets), int(batch), plan, probe, cache
         classes = {}
         for i, n in enumerate(self.nets):
-            classes.setdefault(shape_class(n), []).append(i)
+            if plan in ("auto", "multi") and multi_ok(n):
+                key = ("multi", n.neg_mode)
+            else:
+                key = shape_class(n)
+            classes.setdefault(key, []).append(i)
         self.classes = classes
         self.groups = None
         self.tuning = {}
 
     def _signature(self, key, members):
         cores = sum(self.nets[i].n_cores for i in members)
+        if key[0] == "multi":
+            shapes = sorted({(self.nets[i].axons, self.nets[i].neurons) for i in members})
+            return f"multi-neg{key[1]}-nets{len(members)}-cores{cores}-shapes{shapes}-b{self.batch}"
         return f"path{key[0]}-A{key[1]}-N{key[2]}-neg{key[3]}-fmt{key[4]}-nets{len(members)}-cores{cores}-b{self.batch}"
 
     def _load_cache(self):
@@ -188,31 +229,42 @@ class Sweep:
                 return json.load(f)
         return {}
 
-    def _tune(self, x, window):
+    def _tune_multi(self, g, xp, window):
+        """Times every (weight stages, split costs) candidate on the probe
+        samples (one warm-up run each) and sets the fastest."""
+        _, mx, _, _ = g.sim.tuning()
+        times = {}
+        for stages in range(2, mx + 1):
+            for cm, cs in COST_CANDIDATES:
+                g.sim.set_tuning(stages, cm, cs)
+                g.run(self.nets, xp, window)
+                t0 = time.perf_counter()
+                g.run(self.nets, xp, window)
+                times[f"{stages},{cm},{cs}"] = time.perf_counter() - t0
+        best = min(times, key=times.get)
+        return [int(v) for v in best.split(",")], times
+
+    def _build(self, x, window):
         cached = self._load_cache()
         groups = []
         xp = x[:min(self.probe, x.shape[0])]
         for key, members in self.classes.items():
             sig = self._signature(key, members)
-            if len(members) == 1:
-                choice = "separate"
-            elif self.plan != "auto":
-                choice = self.plan
-            elif sig in cached:
-                choice = cached[sig]["plan"]
-                self.tuning[sig] = dict(cached[sig], cached=True)
-            else:
-                times = {}
-                for cand in ("combined", "separate"):
-                    g = _Group(key, members, self.nets, min(self.batch, xp.shape[0]), cand)
-                    g.run(self.nets, xp, window)  # warm-up
-                    t0 = time.perf_counter()
-                    g.run(self.nets, xp, window)
-                    times[cand] = time.perf_counter() - t0
-                    g.close()
-                choice = min(times, key=times.get)
-                self.tuning[sig] = {"plan": choice, "seconds": times, "probe_samples": int(xp.shape[0])}
-                cached[sig] = self.tuning[sig]
+            if key[0] == "multi":
+                if self.plan == "auto" and sig in cached:
+                    self.tuning[sig] = dict(cached[sig], cached=True)
+                    groups.append(_MultiGroup(key, members, self.nets, self.batch, cached[sig]["choice"]))
+                    continue
+                g = _MultiGroup(key, members, self.nets, self.batch)
+                if self.plan == "auto":
+                    choice, times = self._tune_multi(g, xp, window)
+                    g.sim.set_tuning(*choice)
+                    g.sim.reset()
+                    self.tuning[sig] = {"choice": choice, "seconds": times, "probe_samples": int(xp.shape[0])}
+                    cached[sig] = self.tuning[sig]
+                groups.append(g)
+                continue
+            choice = "separate" if len(members) == 1 else ("combined" if self.plan in ("auto", "multi") else self.plan)
             groups.append(_Group(key, members, self.nets, self.batch, choice))
         if self.cache and self.plan == "auto":
             with open(self.cache, "w") as f:
@@ -224,21 +276,31 @@ class Sweep:
         -> list of per-network counts [S, n_outputs], in network order."""
         x = np.ascontiguousarray(inputs, dtype=np.uint32)
         if self.groups is None:
-            self.groups = self._tune(x, window)
+            self.groups = self._build(x, window)
         out = {}
         for g in self.groups:
             out.update(g.run(self.nets, x, window))
         return [out[i] for i in range(len(self.nets))]
 
     def counters(self):
-        """[n_networks, 4] spikes, packets, outputs, synaptic events since creation."""
+        """[n_networks, 4] spikes, packets, outputs, synaptic events since the
+        handles were created or reset."""
         res = {}
         for g in self.groups or []:
             res.update(g.counters())
         return np.stack([res[i] for i in range(len(self.nets))])
 
+    def reset(self):
+        for g in self.groups or []:
+            g.reset()
+
     def plans(self):
         return [(g.key, g.plan, list(g.members)) for g in self.groups or []]
+
+    def multi_handle(self):
+        """The MultiSim of the multi plan's only handle (None if there is none or several)."""
+        m = [g.sim for g in self.groups or [] if g.plan == "multi"]
+        return m[0] if len(m) == 1 else None
 
     def close(self):
         for g in self.groups or []:

@@ -69,6 +69,17 @@ def test_shape_classes_and_formats(S):
         else:
             assert key[:3] == (ranc.RANC_PATH_PLAIN, n.axons, n.neurons)
             assert key[4] == ranc.RANC_POTENTIAL_INT32
+        assert S.multi_ok(n)  # every core shape of the sweep space fits the multi-network path
+    # the library's storage rule, asked without a device: a threshold past 2048 leaves fp16
+    n = nets[0]
+    assert S.potential_format(n) == ranc.RANC_POTENTIAL_FP16
+    n.pos_thr[0, 0] = 2049
+    assert S.potential_format(n) == ranc.RANC_POTENTIAL_INT16
+    n.neg_thr[0, 0] = -40000
+    assert S.potential_format(n) == ranc.RANC_POTENTIAL_INT32
+    n.weight_bits = 2  # a description ranc_create would reject
+    with pytest.raises(ranc.RancError):
+        S.potential_format(n)
 
 
 # ---------------------------------------------------------------------------
@@ -98,7 +109,9 @@ def test_sweep_runner_matches_each_network(oracle_mod, S, plan):
 
 @pytest.mark.gpu
 def test_autotuned_sweep_caches_its_choice(oracle_mod, S, tmp_path):
-    nets = small_sweep(12, n=6, sizes=(128, 256), core_range=(3, 6))
+    """The auto plan puts every network into one multi-network handle, tunes
+    its pipeline on the probe samples, and reuses the cached choice."""
+    nets = small_sweep(12, n=6, sizes=(128, 256, 512), core_range=(3, 6))
     x = W.rate_coded_inputs(12, 130, 8, 1024, 0.2)
     T = 10
     refs = oracle_members(oracle_mod, nets, x, T)
@@ -108,8 +121,15 @@ def test_autotuned_sweep_caches_its_choice(oracle_mod, S, tmp_path):
         outs = sw.run_samples(x, T)
         for k, (o, r) in enumerate(zip(outs, refs)):
             np.testing.assert_array_equal(o, r["out"], err_msg=f"net {k}")
-        multi = [sig for sig, t in sw.tuning.items()]
-        assert multi, "at least one class has several members and is tuned"
+        cnt = sw.counters()
+        for k, r in enumerate(refs):
+            np.testing.assert_array_equal(cnt[k], r["counters"][:, :4].sum(0), err_msg=f"net {k}")
+        assert [p[1] for p in sw.plans()] == ["multi"] and sw.multi_handle() is not None
+        (sig, t), = sw.tuning.items()
+        stages, cm, cs = t["choice"]
+        assert sw.multi_handle().tuning() == (stages, sw.multi_handle().tuning()[1], cm, cs)
+        max_stages = sw.multi_handle().tuning()[1]
+        assert len(t["seconds"]) == (max_stages - 1) * len(S.COST_CANDIDATES)  # every candidate was timed
         if round_ == 1:
-            assert all(t.get("cached") for t in sw.tuning.values())
+            assert t.get("cached")
         sw.close()
