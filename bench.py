@@ -542,6 +542,59 @@ def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), bat
                                        f"({cpu_s:.1f} s on {thr} threads, one configuration per thread)"}}
 
 
+def bench_xbar(ranc, torch, steps, warmup, batch=4096, p_active=0.2):
+    """The crossbar product of the 512-core MNIST-shaped network (256 x 256
+    cores, 4 axon types, 9-bit weights) for `batch` samples whose axons are
+    active with probability p_active, in each exact tensor-core formulation
+    (include/ranc_xbar.h).  A step is one product over every core and sample
+    (dV digests written, 8 B per (sample, core)); L2 is flushed between steps.
+    The outputs are checked against the crossbar oracle on a sample of cores."""
+    import ranc_workloads as W
+    from oracle import crossbar as X
+    net = W.mnist_512core()
+    S = W.rng.bernoulli(0x5EED, 95, (batch, net.axons), p_active)
+    spikes = torch.from_numpy(W.pack_bits_lsb(S).view(np.int32)).cuda()
+    sums = torch.zeros((batch, net.n_cores), dtype=torch.int64, device="cuda")
+    flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    cores = list(range(0, net.n_cores, 17))
+    ref = X.digest_sums(X.delta_v(net, W.pack_bits_lsb(S[:512]), cores=cores))
+    pk = peaks()
+    flop = 2.0 * batch * net.n_cores * net.axons * net.neurons  # dense-equivalent product
+    names = {0: "f16_folded (tcgen05.mma kind::f16, fp16 folded weights)",
+             1: "f8_per_type (tcgen05.mma kind::f8f6f4, e4m3 0/1, one accumulator per axon type)",
+             2: "i8_mma_sync (mma.sync m16n8k32 s8, 0/1, per-type int32 counts)"}
+    res = {}
+    for form in (0, 1, 2):
+        x = ranc.Xbar(net, form)
+        for _ in range(warmup):
+            x.run(spikes.data_ptr(), batch, 0, sums.data_ptr())
+        x.sync()
+        ms = []
+        for _ in range(steps):
+            flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x.run(spikes.data_ptr(), batch, 0, sums.data_ptr())
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        x.sync()
+        got = sums.cpu().numpy()[:512][:, cores]
+        x.close()
+        t = float(np.median(ms))
+        res[names[form]] = {"ms": t, "dense_equivalent_tflops": flop / (t * 1e-3) / 1e12,
+                            "frac_of_bf16_peak": flop / (t * 1e-3) / 1e12 / pk["bf16_tflops"],
+                            "equal_to_oracle": bool(np.array_equal(got, ref))}
+    best = min(res, key=lambda k: res[k]["ms"])
+    return {"metric": "crossbar product of the 512-core MNIST-shaped net: ms per product, per exact formulation",
+            "unit": "ms", "higher_is_better": False, "steps": steps, "warmup": warmup,
+            "config": {"workload": f"{batch} samples x 512 cores x 256 axons x 256 neurons, axons active with "
+                                   f"p = {p_active}", "l2": "flushed between steps (512 MiB write)"},
+            "forms": res, "fastest": best, "peak_source": pk["source"] + " (bf16_tflops burst)",
+            "parity": {"compared": "digest sum_n (n % 8 + 1) dV of 512 samples x 31 cores vs the crossbar oracle",
+                       "equal": all(v["equal_to_oracle"] for v in res.values())}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,7 +606,7 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream", "sweep"],
+    ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream", "sweep", "xbar"],
                     help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1; "
                          "stream: Table I's streamed 10 010-tick MNIST-512c shape, one frame per tick; "
                          "dse: surrogate-ranked design-space exploration (512 training points, 20000 candidates)")
@@ -603,6 +656,13 @@ def main():
     if args.workload == "stream":
         if rank == 0:
             print(json.dumps(bench_stream(ranc, torch, args.steps, args.warmup)))
+        return
+    if args.workload == "xbar":
+        if rank == 0:
+            line = bench_xbar(ranc, torch, args.steps, args.warmup)
+            print(json.dumps(line))
+            if not line["parity"]["equal"]:
+                sys.exit(1)
         return
     if args.workload == "sweep":
         if rank == 0:

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libranc.so")
-UNITS = ("ranc_api.cu", "ranc_plain.cu", "ranc_batched.cu", "ranc_multi.cu", "ranc_mlp.cu")
+UNITS = ("ranc_api.cu", "ranc_plain.cu", "ranc_batched.cu", "ranc_multi.cu", "ranc_xbar.cu", "ranc_mlp.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -27,6 +27,8 @@ EXPORTED = ("ranc_create", "ranc_create_multi", "ranc_set_multi_tuning", "ranc_g
             "ranc_potential_format", "ranc_desc_potential_format", "ranc_device_allocations", "ranc_destroy",
             "ranc_last_error")
 RANC_POTENTIAL_INT32, RANC_POTENTIAL_INT16, RANC_POTENTIAL_FP16 = 0, 1, 2
+RANC_XBAR_F16_FOLDED, RANC_XBAR_F8_PER_TYPE, RANC_XBAR_I8_MMA_SYNC = 0, 1, 2
+XBAR_EXPORTED = ("ranc_xbar_create", "ranc_xbar_run", "ranc_xbar_sync", "ranc_xbar_destroy", "ranc_xbar_last_error")
 
 
 class RancError(RuntimeError):
@@ -88,6 +90,13 @@ def load_library(path=LIB_PATH):
         "ranc_destroy": ([vp], None),
         "ranc_last_error": ([vp], C.c_char_p),
     }
+    sig.update({  # crossbar-product formulations (include/ranc_xbar.h)
+        "ranc_xbar_create": ([C.POINTER(ranc_desc), i32, vp, C.POINTER(vp)], C.c_int),
+        "ranc_xbar_run": ([vp, vp, i32, vp, vp], C.c_int),
+        "ranc_xbar_sync": ([vp], C.c_int),
+        "ranc_xbar_destroy": ([vp], None),
+        "ranc_xbar_last_error": ([vp], C.c_char_p),
+    })
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes, f.restype = args, res
@@ -482,6 +491,43 @@ class MultiSim:
     def close(self):
         if self.h is not None:
             ranc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _xcheck(rc, h):
+    if rc != RANC_OK:
+        raise RancError(rc, _lib.ranc_xbar_last_error(h).decode())
+
+
+class Xbar:
+    """Crossbar products dV [B][C][N] of ``net``'s cores in one of the exact
+    tensor-core formulations (RANC_XBAR_*; include/ranc_xbar.h)."""
+
+    def __init__(self, net, form, stream=0):
+        self.net, self.form = net, int(form)
+        d, keep = _desc(net)
+        h = C.c_void_p()
+        _xcheck(_lib.ranc_xbar_create(C.byref(d), self.form, C.c_void_p(int(stream)), C.byref(h)), None)
+        self.h = h
+
+    def run(self, spikes_dev, batch, dv_dev=0, sums_dev=0):
+        """Device pointers: spikes [batch][A/32] uint32, dv [batch][C][N] int32
+        (0: not written), sums [batch][C] int64 (0: not written)."""
+        _xcheck(_lib.ranc_xbar_run(self.h, C.c_void_p(int(spikes_dev)), int(batch), C.c_void_p(int(dv_dev) or None),
+                                   C.c_void_p(int(sums_dev) or None)), self.h)
+
+    def sync(self):
+        _xcheck(_lib.ranc_xbar_sync(self.h), self.h)
+
+    def close(self):
+        if self.h is not None:
+            _lib.ranc_xbar_destroy(self.h)
             self.h = None
 
     def __del__(self):

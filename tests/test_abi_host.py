@@ -40,6 +40,19 @@ def test_surrogate_header_is_exported(ranc):
     assert sorted(mlp.EXPORTED) == names
 
 
+def test_crossbar_header_is_exported(ranc):
+    xbar_header = os.path.join(ROOT, "include", "ranc_xbar.h")
+    lib = C.CDLL(ranc.LIB_PATH)
+    names = declared_functions(xbar_header)
+    assert names and all(hasattr(lib, n) for n in names)
+    assert sorted(ranc.XBAR_EXPORTED) == names
+
+
+def test_every_header_is_checked():
+    """Each header under include/ is covered by one of the export tests."""
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["ranc.h", "ranc_mlp.h", "ranc_xbar.h"]
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("ranc_create", "ranc_load_inputs", "ranc_step", "ranc_read_outputs", "ranc_destroy"):
