@@ -8,8 +8,11 @@
  * but trains no model; this is the project's own component.
  *
  * Numerics: weights are held as bf16 for the forward and backward passes, with
- * fp32 master copies updated by Adam; every product is accumulated in fp32;
- * activations and gradients are fp32.  The loss is the mean squared error over
+ * fp32 master copies updated by Adam; activations and gradients are fp32.
+ * Every matrix product runs on the tensor cores (mma.sync bf16 -> fp32
+ * accumulation): a bf16 weight enters exactly, an fp32 activation or gradient
+ * as two bf16 terms hi + lo (16 significant bits), and a product of two fp32
+ * operands as hi*hi + hi*lo + lo*hi.  The loss is the mean squared error over
  * the batch and the outputs.
  *
  * Conventions as in ranc.h: 0 or a negative RANC_E* code, reason in

@@ -1,14 +1,19 @@
 // Design-space surrogate: forward, MSE backward and Adam for a small fully
 // connected network (see include/ranc_mlp.h).  bf16 weights in the passes,
-// fp32 accumulation, fp32 masters and optimizer state.  The layers are at most
-// 1024 wide and the batches a few hundred rows, so each kernel maps one thread
-// to one output element and sums in a fixed order (deterministic results).
+// fp32 accumulation, fp32 masters and optimizer state.  Every matrix product
+// (forward, gradient of the inputs, gradient of the weights) runs on the
+// tensor cores with mma.sync.m16n8k16 bf16 -> fp32: an fp32 operand enters as
+// two bf16 terms x = hi + lo (hi = bf16(x), lo = bf16(x - hi): 16 significant
+// bits), a product of two such operands as hi*hi + hi*lo + lo*hi; bf16
+// weights enter exactly.  Tiles and the order of the sums are fixed, so the
+// results are deterministic.
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -64,21 +69,123 @@ thread_local std::string g_mlp_create_error;
         if (e_ != cudaSuccess) return mlp_fail((m), RANC_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
     } while (0)
 
-// Z = X W^T + b (and A = relu(Z) when relu), one thread per output element.
-__global__ void linear_fwd(const float *X, const __nv_bfloat16 *W, const float *bias, int batch, int in, int out,
-                           int relu, float *Z, float *A) {
-    extern __shared__ float xs[];
-    const int b = blockIdx.y;
-    for (int i = threadIdx.x; i < in; i += blockDim.x) xs[i] = X[(size_t)b * in + i];
-    __syncthreads();
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= out || b >= batch) return;
-    const __nv_bfloat16 *w = W + (size_t)o * in;
-    float acc = bias[o];
-    for (int i = 0; i < in; ++i) acc = fmaf(xs[i], __bfloat162float(w[i]), acc);
-    Z[(size_t)b * out + o] = acc;
-    A[(size_t)b * out + o] = relu ? fmaxf(acc, 0.f) : acc;
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM: C[m][n] = sum_k A(m, k) * B(n, k) for the three products
+// of a layer, with strided operands (element (m, k) of A at A[m * am + k * ak],
+// element (n, k) of B at B[n * bn + k * bk]).  A CTA (4 warps) computes a 64 x
+// 64 tile of C over K-tiles of 32: the operands are staged in shared memory as
+// bf16 (hi and lo terms of fp32 operands), each warp holds a 32 x 32 block as
+// 2 x 4 m16n8 accumulators and issues mma.sync.m16n8k16 per K-step.
+// ---------------------------------------------------------------------------
+
+constexpr int kGM = 64, kGN = 64, kGK = 32, kGPad = 40;  // tile sizes; shared rows of 40 bf16 (no bank conflicts)
+
+enum { kEpiForward = 0, kEpiMaskRelu = 1, kEpiStore = 2 };
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
+
+template <typename T>
+__device__ __forceinline__ float as_f32(T x) {
+    if constexpr (std::is_same<T, float>::value) return x;
+    else return __bfloat162float(x);
+}
+
+// Epilogues: forward (C + bias -> Z, relu or identity -> Act), gradient of
+// the inputs (C * (Z > 0)), plain store.
+template <typename TB, bool kSplitB, int kEpi>
+__global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const float *A, long long am, long long ak, const TB *B,
+                                               long long bn, long long bk, float *C, const float *bias, int relu,
+                                               float *Act, const float *Zmask) {
+    __shared__ __align__(16) __nv_bfloat16 sa[2][kGM][kGPad], sb[2][kGN][kGPad];  // [hi / lo][row][k]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+    const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kGK) {
+        for (int idx = tid; idx < kGM * kGK; idx += 128) {
+            const int r = idx / kGK, kk = idx % kGK, m = m0 + r, k = k0 + kk;
+            const float x = (m < M && k < K) ? A[(long long)m * am + (long long)k * ak] : 0.f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            sa[0][r][kk] = hi;
+            sa[1][r][kk] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+        for (int idx = tid; idx < kGN * kGK; idx += 128) {
+            const int r = idx / kGK, kk = idx % kGK, n = n0 + r, k = k0 + kk;
+            const float x = (n < N && k < K) ? as_f32(B[(long long)n * bn + (long long)k * bk]) : 0.f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            sb[0][r][kk] = hi;
+            if constexpr (kSplitB) sb[1][r][kk] = __float2bfloat16_rn(x - __bfloat162float(hi));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < kGK; ks += 16) {
+            uint32_t af[2][2][4], bf[2][4][2];  // [hi / lo][tile][regs]
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int r = wm + 16 * i + g;
+                    af[h][i][0] = *reinterpret_cast<const uint32_t *>(&sa[h][r][ks + 2 * tq]);
+                    af[h][i][1] = *reinterpret_cast<const uint32_t *>(&sa[h][r + 8][ks + 2 * tq]);
+                    af[h][i][2] = *reinterpret_cast<const uint32_t *>(&sa[h][r][ks + 2 * tq + 8]);
+                    af[h][i][3] = *reinterpret_cast<const uint32_t *>(&sa[h][r + 8][ks + 2 * tq + 8]);
+                }
+                if (h == 1 && !kSplitB) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = wn + 8 * j + g;
+                    bf[h][j][0] = *reinterpret_cast<const uint32_t *>(&sb[h][r][ks + 2 * tq]);
+                    bf[h][j][1] = *reinterpret_cast<const uint32_t *>(&sb[h][r][ks + 2 * tq + 8]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    mma_bf16(acc[i][j], af[0][i][0], af[0][i][1], af[0][i][2], af[0][i][3], bf[0][j][0], bf[0][j][1]);
+                    mma_bf16(acc[i][j], af[1][i][0], af[1][i][1], af[1][i][2], af[1][i][3], bf[0][j][0], bf[0][j][1]);
+                    if constexpr (kSplitB)
+                        mma_bf16(acc[i][j], af[0][i][0], af[0][i][1], af[0][i][2], af[0][i][3], bf[1][j][0], bf[1][j][1]);
+                }
+        }
+        __syncthreads();
+    }
+    // accumulator element e of tile (i, j): row wm + 16 i + g + 8 (e / 2), column wn + 8 j + 2 tq + e % 2
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm + 16 * i + g + 8 * (e >> 1), n = n0 + wn + 8 * j + 2 * tq + (e & 1);
+                if (m >= M || n >= N) continue;
+                const size_t o = (size_t)m * N + n;
+                float v = acc[i][j][e];
+                if constexpr (kEpi == kEpiForward) {
+                    v += bias[n];
+                    C[o] = v;
+                    Act[o] = relu ? fmaxf(v, 0.f) : v;
+                } else if constexpr (kEpi == kEpiMaskRelu) {
+                    C[o] = Zmask[o] > 0.f ? v : 0.f;
+                } else {
+                    C[o] = v;
+                }
+            }
+}
+
+dim3 gemm_grid(int M, int N) { return dim3((N + kGN - 1) / kGN, (M + kGM - 1) / kGM); }
 
 // dY = 2 (y - t) / (batch * d); loss = mean (y - t)^2 summed per row then over rows.
 __global__ void mse_grad(const float *Y, const float *T, int batch, int d, float *dY, float *row_loss) {
@@ -102,32 +209,13 @@ __global__ void sum_rows(const float *row_loss, int batch, float *loss) {
     }
 }
 
-// dW[o][i] = sum_b dZ[b][o] * Xin[b][i];  db[o] = sum_b dZ[b][o].
-__global__ void linear_bwd_weight(const float *dZ, const float *Xin, int batch, int in, int out, float *dW,
-                                  float *db) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < out * in) {
-        const int o = idx / in, i = idx % in;
-        float acc = 0.f;
-        for (int b = 0; b < batch; ++b) acc = fmaf(dZ[(size_t)b * out + o], Xin[(size_t)b * in + i], acc);
-        dW[idx] = acc;
-    }
-    if (idx < out) {
-        float acc = 0.f;
-        for (int b = 0; b < batch; ++b) acc += dZ[(size_t)b * out + idx];
-        db[idx] = acc;
-    }
-}
-
-// dZprev[b][i] = (sum_o dZ[b][o] * W[o][i]) * (Zprev[b][i] > 0).
-__global__ void linear_bwd_data(const float *dZ, const __nv_bfloat16 *W, const float *Zprev, int batch, int in,
-                                int out, float *dZprev) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= batch * in) return;
-    const int b = idx / in, i = idx % in;
+// db[o] = sum_b dZ[b][o] (fixed order).
+__global__ void bias_grad(const float *dZ, int batch, int out, float *db) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= out) return;
     float acc = 0.f;
-    for (int o = 0; o < out; ++o) acc = fmaf(dZ[(size_t)b * out + o], __bfloat162float(W[(size_t)o * in + i]), acc);
-    dZprev[idx] = Zprev[idx] > 0.f ? acc : 0.f;
+    for (int b = 0; b < batch; ++b) acc += dZ[(size_t)b * out + o];
+    db[o] = acc;
 }
 
 __global__ void adam_kernel(float *p, const float *g, float *m1, float *m2, __nv_bfloat16 *w16, const char *is_w,
@@ -180,9 +268,10 @@ int mlp_forward(ranc_mlp *m, const float *x, int batch) {
     const float *in = x;
     for (int l = 0; l < m->n_layers; ++l) {
         const Layer &L = m->layers[l];
-        dim3 grid((L.out + 127) / 128, batch);
-        linear_fwd<<<grid, 128, L.in * sizeof(float), m->stream>>>(in, m->w16 + L.w_off, m->p + L.b_off, batch, L.in,
-                                                                   L.out, l + 1 < m->n_layers, m->Z[l], m->A[l]);
+        // Z[b][o] = sum_i X[b][i] W[o][i] + bias[o]
+        gemm_tc<__nv_bfloat16, false, kEpiForward><<<gemm_grid(batch, L.out), 128, 0, m->stream>>>(
+            batch, L.out, L.in, in, L.in, 1, m->w16 + L.w_off, L.in, 1, m->Z[l], m->p + L.b_off, l + 1 < m->n_layers,
+            m->A[l], nullptr);
         MLP_CUDA(m, cudaGetLastError());
         in = m->A[l];
     }
@@ -336,13 +425,16 @@ extern "C" int ranc_mlp_loss_backward(ranc_mlp *m, const float *x, const float *
     for (int l = L_last; l >= 0; --l) {
         const Layer &L = m->layers[l];
         const float *xin = l > 0 ? m->A[l - 1] : x;
-        const int nw = L.in * L.out;
-        linear_bwd_weight<<<(nw + 255) / 256, 256, 0, m->stream>>>(dz, xin, batch, L.in, L.out, m->g + L.w_off,
-                                                                   m->g + L.b_off);
+        // dW[o][i] = sum_b dZ[b][o] Xin[b][i]: A(o, b) = dZ[b][o], B(i, b) = Xin[b][i]
+        gemm_tc<float, true, kEpiStore><<<gemm_grid(L.out, L.in), 128, 0, m->stream>>>(
+            L.out, L.in, batch, dz, 1, L.out, xin, 1, L.in, m->g + L.w_off, nullptr, 0, nullptr, nullptr);
+        MLP_CUDA(m, cudaGetLastError());
+        bias_grad<<<(L.out + 127) / 128, 128, 0, m->stream>>>(dz, batch, L.out, m->g + L.b_off);
         MLP_CUDA(m, cudaGetLastError());
         if (l > 0) {
-            linear_bwd_data<<<(batch * L.in + 255) / 256, 256, 0, m->stream>>>(dz, m->w16 + L.w_off, m->Z[l - 1],
-                                                                               batch, L.in, L.out, dz_prev);
+            // dZprev[b][i] = (sum_o dZ[b][o] W[o][i]) (Zprev[b][i] > 0): A(b, o) = dZ[b][o], B(i, o) = W[o][i]
+            gemm_tc<__nv_bfloat16, false, kEpiMaskRelu><<<gemm_grid(batch, L.in), 128, 0, m->stream>>>(
+                batch, L.in, L.out, dz, L.out, 1, m->w16 + L.w_off, 1, L.in, dz_prev, nullptr, 0, nullptr, m->Z[l - 1]);
             MLP_CUDA(m, cudaGetLastError());
             std::swap(dz, dz_prev);
         }

@@ -760,14 +760,19 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
                 const uint32_t *row = d->crossbar + ((size_t)c * A + ax) * NWd;
                 const int k = d->axon_type[(size_t)c * A + ax];
                 const int kb = ax >> 6, q16 = (ax & 63) >> 3, e8 = ax & 7;
-                for (int nn = 0; nn < N; nn++) {
-                    const bool on = (row[nn >> 5] >> (nn & 31)) & 1u;
-                    od[(size_t)sd.aoff + (size_t)c * A + ax] += on ? 1u : 0u;
-                    if (!on) continue;
-                    const int h = nn >> 7, r = nn & 127;
-                    const size_t blk = (size_t)sd.woff + ((size_t)c * sd.NH + h) * sd.KB + kb;
-                    const __half hv = __float2half((float)d->weight[((size_t)c * K + k) * N + nn]);
-                    wb[blk * (kBlk / 2) + (size_t)r * 64 + ((q16 ^ (r & 7)) << 3) + e8] = *reinterpret_cast<const uint16_t *>(&hv);
+                const int16_t *wrow = d->weight + ((size_t)c * K + k) * N;
+                for (int wd = 0; wd < NWd; wd++) {  // the connections of this axon, word by word
+                    uint32_t bits = row[wd];
+                    od[(size_t)sd.aoff + (size_t)c * A + ax] += (uint32_t)__builtin_popcount(bits);
+                    while (bits) {
+                        const int nn = wd * 32 + __builtin_ctz(bits);
+                        bits &= bits - 1u;
+                        const int h = nn >> 7, r = nn & 127;
+                        const size_t blk = (size_t)sd.woff + ((size_t)c * sd.NH + h) * sd.KB + kb;
+                        const __half hv = __float2half((float)wrow[nn]);
+                        wb[blk * (kBlk / 2) + (size_t)r * 64 + ((q16 ^ (r & 7)) << 3) + e8] =
+                            *reinterpret_cast<const uint16_t *>(&hv);
+                    }
                 }
             }
         }
