@@ -225,7 +225,56 @@ int fold_timing(ranc_sim *sim) {
     return RANC_OK;
 }
 
+PlainArgs plain_args(const ranc_sim *sim) {
+    PlainArgs a{};
+    a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
+    a.B = sim->B; a.n_valid = sim->n_valid; a.in_words = sim->in_words; a.in_ticks = sim->in_ticks;
+    a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = sim->tick;
+    a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
+    a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon;
+    a.inputs = sim->in_override ? sim->in_override : sim->inputs;
+    a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
+    a.stall_test = sim->stall_test;
+    a.olog = sim->olog_t; a.olog_stride = sim->olog_stride;
+    return a;
+}
+
+// Plain path, several ticks without a per-tick output log: one persistent
+// cooperative launch (plain_steps_kernel).  RANC_ENOTSUP when it cannot run.
+int step_plain_persistent(ranc_sim *sim, int n_ticks) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (sim->timing) {
+        if (sim->ev_used + 2 > 4096) {
+            int rc = fold_timing(sim);
+            if (rc) return rc;
+        }
+        e0 = next_event(sim);
+        e1 = next_event(sim);
+        if (!e0 || !e1) return fail(sim, RANC_ECUDA, "cudaEventCreate failed");
+        CUDA_OR_FAIL(sim, cudaEventRecord(e0, sim->stream));
+    }
+    cudaError_t e = launch_plain_steps(plain_args(sim), n_ticks, sim->gbar, sim->stream);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        if (sim->timing) sim->ev_used -= 2;
+        return RANC_ENOTSUP;
+    }
+    if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "persistent tick kernel: %s", cudaGetErrorString(e));
+    if (sim->timing) {
+        CUDA_OR_FAIL(sim, cudaEventRecord(e1, sim->stream));
+        sim->ev_ticks.push_back(n_ticks);
+    }
+    sim->launches++;
+    sim->tick += n_ticks;
+    sim->ticks_total += (unsigned long long)sim->n_valid * n_ticks;
+    return RANC_OK;
+}
+
 int step_ticks(ranc_sim *sim, int n_ticks) {
+    if (sim->path == RANC_PATH_PLAIN && n_ticks >= 2 && !sim->olog_t) {
+        int rc = step_plain_persistent(sim, n_ticks);
+        if (rc != RANC_ENOTSUP) return rc;
+    }
     for (int t = 0; t < n_ticks; t++) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (sim->timing) {
@@ -240,17 +289,7 @@ int step_ticks(ranc_sim *sim, int n_ticks) {
         }
         cudaError_t e;
         if (sim->path == RANC_PATH_PLAIN) {
-            PlainArgs a{};
-            a.C = sim->C; a.A = sim->A; a.N = sim->N; a.K = sim->K; a.AW = sim->A / 32; a.NW = sim->N / 32;
-            a.B = sim->B; a.n_valid = sim->n_valid; a.in_words = sim->in_words; a.in_ticks = sim->in_ticks;
-            a.n_out = sim->n_outputs; a.neg_mode = sim->neg_mode; a.tick = sim->tick;
-            a.xbarT = sim->xbarT; a.wtype = sim->wtype; a.axperm = sim->axperm; a.SW = sim->SW; a.wnk = sim->wnk; a.prm = sim->prm; a.dst = sim->dst;
-            a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon;
-            a.inputs = sim->in_override ? sim->in_override : sim->inputs;
-            a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
-            a.stall_test = sim->stall_test;
-            a.olog = sim->olog_t; a.olog_stride = sim->olog_stride;
-            e = launch_plain_tick(a, sim->stream);
+            e = launch_plain_tick(plain_args(sim), sim->stream);
         } else {
             BatchedArgs a{};
             a.tick = sim->tick;

@@ -200,6 +200,7 @@ cudaError_t launch_plain_tick(const PlainArgs &a, cudaStream_t s);
 cudaError_t raise_smem_limit(const void *kernel, int bytes);
 cudaError_t plain_setup_kernel_attrs(int N, int SW);
 cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s);
+cudaError_t launch_plain_steps(const PlainArgs &a, int n_ticks, unsigned *bar, cudaStream_t s);
 cudaError_t launch_plain_reset(ranc_sim *sim, bool counters);
 cudaError_t launch_digest(const int *V, long long n, unsigned long long *out, cudaStream_t s);
 // Implemented in ranc_batched.cu

@@ -18,6 +18,8 @@
 // the launch has no read/write race; OR and integer addition are order
 // independent, so the result does not depend on scheduling.
 
+#include <algorithm>
+
 #include "ranc_internal.cuh"
 #include "ranc_ptx.cuh"
 
@@ -426,6 +428,184 @@ cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     if ((e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
     void *args[] = {const_cast<WindowArgs *>(&w)};
     return cudaLaunchCooperativeKernel((const void *)plain_window_kernel, dim3(grid), dim3(threads), args, smem, s);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of ranc_step on the plain path: n ticks in one cooperative
+// launch, for grids of any size.  Work units are (sample, core) pairs, dealt
+// to the CTAs in turn (the same ones every tick); ticks are separated by the
+// grid barrier.  A CTA (1024 threads) runs each tick in phases over all its
+// units at once, so that the loads of many units are in flight together:
+//   A  scheduler rows read and cleared, input lines ORed in, activity flags;
+//   B  crossbar integration of the active units, one at a time (crossbar
+//      words read from global memory / L2, type-sorted as in plain_tick_kernel);
+//   C  leak, thresholds and reset of every neuron of every unit, four at a
+//      time per thread with their loads issued first; spike words, delivery,
+//      output bus, counters.
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxStepUnits = 64;  // units per CTA and tick held in shared memory
+
+__global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a, int n_ticks, unsigned *bar) {
+    extern __shared__ __align__(16) uint32_t smp[];
+    __shared__ uint32_t red[kMaxStepUnits][4];
+    __shared__ int act_sh[kMaxStepUnits];
+    __shared__ int s_ok;
+    const int N = a.N, AW = a.AW, SW = a.SW, C = a.C;
+    const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
+    const int n_units = C * a.B;
+    const int m = (n_units - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // units of this CTA
+    int *dvs = reinterpret_cast<int *>(smp);                        // [m][N] dV of the active units
+    uint32_t *sb = reinterpret_cast<uint32_t *>(dvs + (size_t)m * N);  // [m][AW] active axons
+    uint32_t *spb = sb + m * AW;                                    // [SW] sorted active axons of one unit
+    uint16_t *perm = reinterpret_cast<uint16_t *>(spb + SW);        // [SW * 32]
+    int8_t *wt = reinterpret_cast<int8_t *>(perm + SW * 32);        // [SW]
+    auto unit = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };  // b * C + c
+    unsigned gen = 0;
+    if (tid == 0) s_ok = 1;
+    for (int t = 0; t < n_ticks; ++t) {
+        const long long tick = a.tick + t;
+        const int r0 = (int)(tick & (kRows - 1));
+        // ---- A: rows, inputs, activity
+        for (int i = tid; i < m * 4; i += nt) red[i / 4][i % 4] = 0u;
+        for (int i = tid; i < m; i += nt) act_sh[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < m * AW; i += nt) {
+            uint32_t *row = a.ring + ((size_t)unit(i / AW) * kRows + r0) * AW + i % AW;
+            const uint32_t w = *row;
+            sb[i] = w;
+            if (w) {
+                *row = 0u;
+                act_sh[i / AW] = 1;
+            }
+        }
+        __syncthreads();
+        if (tick < a.in_ticks) {
+            for (int i = 0; i < m; ++i) {
+                const int u = unit(i), b = u / C, c = u % C;
+                if (b >= a.n_valid) continue;
+                const uint32_t *in = a.inputs + ((size_t)b * a.in_ticks + tick) * a.in_words;
+                for (int k = a.in_ptr[c] + tid; k < a.in_ptr[c + 1]; k += nt) {
+                    const int L = a.in_line[k];
+                    if ((in[L >> 5] >> (L & 31)) & 1u) {
+                        const int ax = a.in_axon[k];
+                        atomicOr(&sb[i * AW + (ax >> 5)], 1u << (ax & 31));
+                        act_sh[i] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // ---- B: integration of the active units
+        for (int i = 0; i < m; ++i) {
+            if (!act_sh[i]) continue;  // uniform over the CTA
+            const int c = unit(i) % C;
+            for (int k = tid; k < SW * 32; k += nt) perm[k] = a.axperm[(size_t)c * SW * 32 + k];
+            for (int k = tid; k < SW; k += nt) wt[k] = a.wtype[(size_t)c * SW + k];
+            __syncthreads();
+            if (tid < ((SW * 32 + 31) & ~31)) gather_sorted(sb + i * AW, perm, AW, SW, 1, spb, tid, nt);
+            __syncthreads();
+            for (int n = tid; n < N; n += nt) {
+                const int4 wv = reinterpret_cast<const int4 *>(a.wnk)[(size_t)c * N + n];
+                const uint32_t wr[4] = {(uint32_t)wv.x, (uint32_t)wv.y, (uint32_t)wv.z, (uint32_t)wv.w};
+                uint32_t syn = 0u;
+                dvs[i * N + n] = integrate_sorted(spb, a.xbarT + (size_t)c * SW * N + n, N, wt, SW, wr, syn);
+                syn = __reduce_add_sync(0xffffffffu, syn);
+                if (lane == 0 && syn) atomicAdd(&red[i][3], syn);
+            }
+            __syncthreads();
+        }
+        // ---- C: neuron updates of every unit, four per thread per round
+        for (int base = tid; base < m * N; base += 4 * nt) {
+            int vv[4];
+            int4 pr[4];
+            int *vp[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = base + q * nt;
+                if (idx >= m * N) break;
+                const int i = idx / N, n = idx % N, u = unit(i), c = u % C;
+                vp[q] = a.V + (size_t)u * N + n;
+                vv[q] = *vp[q];
+                pr[q] = a.prm[(size_t)c * N + n];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int idx = base + q * nt;
+                if (idx >= m * N) break;  // uniform per warp (N is a multiple of 32)
+                const int i = idx / N, n = idx % N, u = unit(i), b = u / C, c = u % C;
+                int v = vv[q] + (act_sh[i] ? dvs[i * N + n] : 0) + pr[q].x;
+                const bool fire = v >= pr[q].y;
+                if (fire)
+                    v = pr[q].w;
+                else if (v < pr[q].z)
+                    v = a.neg_mode ? pr[q].w : pr[q].z;
+                *vp[q] = v;
+                const unsigned fm = __ballot_sync(0xffffffffu, fire);
+                if (lane == 0) a.spk[(size_t)u * a.NW + n / 32] = fm;
+                uint32_t kind = 0u;
+                if (fire) {
+                    const uint2 d = a.dst[(size_t)c * N + n];
+                    kind = dest_kind(d);
+                    if (kind == RANC_DEST_CORE) {
+                        const uint32_t ax = dest_axon(d);
+                        const long long r = (tick + dest_delay(d)) & (kRows - 1);
+                        atomicOr(a.ring + (((size_t)b * C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
+                    } else if (kind == RANC_DEST_OUTPUT) {
+                        atomicAdd(a.out + (size_t)b * a.n_out + d.x, 1u);
+                    }
+                }
+                if (fm) {
+                    const unsigned pm = __ballot_sync(0xffffffffu, kind == RANC_DEST_CORE);
+                    const unsigned om = __ballot_sync(0xffffffffu, kind == RANC_DEST_OUTPUT);
+                    if (lane == 0) {
+                        atomicAdd(&red[i][0], (uint32_t)__popc(fm));
+                        if (pm) atomicAdd(&red[i][1], (uint32_t)__popc(pm));
+                        if (om) atomicAdd(&red[i][2], (uint32_t)__popc(om));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < m * 4; i += nt) {
+            const int u = unit(i / 4);
+            if (u / C < a.n_valid && red[i / 4][i % 4]) a.cnt[(size_t)u * 4 + i % 4] += red[i / 4][i % 4];
+        }
+        // Failure-detection test: CTA 0 does not arrive at the first barrier.
+        if (!grid_sync(bar, gridDim.x, gen, &s_ok, a.stall_test && blockIdx.x == 0 && t == 0)) {
+            if (tid == 0) atomicExch(a.err, kErrTimeout);
+            return;
+        }
+    }
+}
+
+size_t plain_steps_smem(int m, int N, int AW, int SW) {
+    return (size_t)m * N * 4 + (size_t)m * AW * 4 + (size_t)SW * 4 + (size_t)SW * 32 * 2 + (size_t)SW + 16;
+}
+
+// n_ticks ticks of the plain path in one cooperative launch; the grid is the
+// number of CTAs that fit on the device at once, and at least as many as
+// needed for kMaxStepUnits units per CTA (otherwise cudaErrorCooperativeLaunchTooLarge).
+cudaError_t launch_plain_steps(const PlainArgs &a, int n_ticks, unsigned *bar, cudaStream_t s) {
+    const int threads = 1024;
+    const long long units = (long long)a.C * a.B;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const long long grid = std::min<long long>(units, n_sm);  // one CTA per SM
+    const int m = (int)((units + grid - 1) / grid);
+    if (m > kMaxStepUnits) return cudaErrorCooperativeLaunchTooLarge;
+    const size_t smem = plain_steps_smem(m, a.N, a.AW, a.SW);
+    if (smem > 200 * 1024) return cudaErrorCooperativeLaunchTooLarge;  // per-tick launches instead
+    if ((e = raise_smem_limit((const void *)plain_steps_kernel, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plain_steps_kernel, threads, smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
+    PlainArgs args = a;
+    void *params[] = {&args, &n_ticks, &bar};
+    return cudaLaunchCooperativeKernel((const void *)plain_steps_kernel, dim3((unsigned)grid), dim3(threads), params, smem, s);
 }
 
 // V <- v0 for every sample.

@@ -179,13 +179,50 @@ def test_kernel_timing_and_launch_count(ranc):
     sim = ranc.Sim(net, 2, ranc.RANC_PATH_PLAIN)
     n0 = ranc.ranc_launch_count(sim.h)
     ranc.ranc_set_kernel_timing(sim.h, True)
-    sim.step(10)
+    sim.step(10)  # one persistent launch for the 10 ticks
     ms, n = ranc.ranc_read_kernel_timing(sim.h)
     assert n == 10 and ms > 0
-    assert ranc.ranc_launch_count(sim.h) - n0 == 10
+    assert ranc.ranc_launch_count(sim.h) - n0 == 1
+    for _ in range(3):
+        sim.step(1)  # one per-tick launch each
+    ms, n = ranc.ranc_read_kernel_timing(sim.h)
+    assert n == 13 and ranc.ranc_launch_count(sim.h) - n0 == 4
     # one persistent launch for 5 samples in windows of 9 ticks (3 windows of batch 2)
     ranc.ranc_set_kernel_timing(sim.h, True)
     sim.run_samples(W.rate_coded_inputs(1, 5, 8, 784, 0.15), 9)
     ms, n = ranc.ranc_read_kernel_timing(sim.h)
     assert n == 27 and ms > 0
     sim.close()
+
+
+def test_persistent_steps_with_more_units_than_ctas(ranc, oracle_mod):
+    """ranc_step(n) on the plain path runs n ticks in one persistent launch
+    whose CTAs serve several (sample, core group) units each: a 64 x 64 grid
+    of 32 x 32 cores, 4 samples (512 units), against the oracle and against
+    per-tick launches, with checks in the middle of the run."""
+    net = W.random_net(77, 64, 64, axons=32, neurons=32, n_types=4, delay_max=6, n_inputs=300,
+                       fanout_per_line=8, p_core=0.6, p_out=0.2, w_lim=7, weight_bits=4, pthr=(1, 12),
+                       nthr=(-12, -1), leak=(-2, 1), v0=(-2, 2))
+    B, T = 4, 14
+    x = W.rate_coded_inputs(5, B, 10, net.n_inputs, 0.3)
+    ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
+    a = ranc.Sim(net, B, ranc.RANC_PATH_PLAIN)
+    b = ranc.Sim(net, B, ranc.RANC_PATH_PLAIN)
+    for s in (a, b):
+        s.load_inputs(x)
+    t = 0
+    for k in (5, 2, 7):
+        a.step(k)
+        for _ in range(k):
+            b.step(1)
+        t += k
+        va, sa, da = a.state()
+        np.testing.assert_array_equal(va, ref["v_trace"][:, t - 1], err_msg=f"tick {t - 1}")
+        np.testing.assert_array_equal(unpack_spikes(sa, 32), ref["spike_trace"][:, t - 1])
+        assert da == b.state()[2]
+    np.testing.assert_array_equal(a.outputs(), ref["out"])
+    np.testing.assert_array_equal(a.counters()[:4], ref["counters"][:, :4].sum(0))
+    np.testing.assert_array_equal(a.counters(), b.counters())
+    assert ref["counters"][:, 1].sum() > 0
+    a.close()
+    b.close()
