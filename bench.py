@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 # traffic is that times the units it updates.  Valid only for the tick
 # kernel's source it was taken on (kernel_source_sha; see
 # profiles/batched_tick_kernel_mnist512_1024samples.md).
-PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "53b77895a4b86674", "bytes": 393.664000e6 + 236.722432e6,
+PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "f421bcd4bd391697", "bytes": 393.671168e6 + 236.810240e6,
                     "units": 1024 * 512}
 
 
@@ -237,21 +237,39 @@ def batched_bytes_per_sample_core_tick(net, vbytes, active=True):
     return 2 * N * vbytes + N // 8 + (2 * A // 8 if active else 0)
 
 
-def measure_l2_copy(torch, mib=16, reps=200):
+def measure_l2_copy(torch, mib=48, reps=40):
     """Copy bandwidth of a working set that stays in L2 (two buffers of `mib`
-    MiB, read + write bytes), CUDA events: the ceiling for a kernel whose
-    state is L2-resident."""
+    MiB, read + write bytes), `reps` copies replayed as one CUDA graph (no
+    launch gaps), CUDA events: the ceiling for a kernel whose state is
+    L2-resident."""
     a = torch.ones(mib << 18, dtype=torch.float32, device="cuda")
     b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.copy_(a)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            b.copy_(a)
+    g.replay()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(reps):
-        b.copy_(a)
+    g.replay()
     e1.record()
     e1.synchronize()
     return 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+
+# L2 traffic (lts__t_bytes.sum) per tick of the persistent plain window kernel
+# at batch 1 on the 512-core workload, from one ncu capture of 20 windows x 24
+# ticks (profiles/plain_window_kernel_mnist512_b1.md): crossbars stay in shared
+# memory and parameters in registers, so a tick moves far fewer bytes than the
+# per-tick kernel's algorithmic bytes.
+PLAIN_L2_BYTES_PER_TICK = 521356224 / 480
 
 
 def oracle_outputs(net, x, n):
@@ -262,12 +280,16 @@ def oracle_outputs(net, x, n):
 
 
 def parity_check(ref, **runs):
-    """Bit-for-bit comparison of each run's first len(ref) output-bus counts
-    with the oracle's."""
+    """Bit-for-bit comparison of each run's first samples (as many as both the
+    run and the oracle have) with the oracle's output-bus counts."""
     n = ref.shape[0]
     res = {"compared": "output-bus counts per (sample, id) vs the CPU oracle", "samples": int(n)}
     for name, c in runs.items():
-        res[name] = bool(np.array_equal(np.asarray(c)[:n].view(np.uint32), ref.astype(np.uint32)))
+        c = np.asarray(c)
+        k = min(n, c.shape[0])
+        res[name] = bool(k > 0 and np.array_equal(c[:k].view(np.uint32), ref[:k].astype(np.uint32)))
+        if k < n:
+            res[name + "_samples"] = int(k)
     res["equal"] = all(res[k] for k in runs)
     return res
 
@@ -501,14 +523,16 @@ def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), bat
     T = -(-batch // 128)
     nl = max(steps * window, 1)
     bytes_launch = 0.0
-    units = 0.0
+    units = units_act = 0.0
     for k, n in enumerate(nets):
         act, idle = ic[k]
         bytes_launch += (act + idle) * 128 * (2 * n.neurons * vb + n.neurons // 8) + act * 128 * (2 * n.axons // 8)
         bytes_launch += act / T * n.axons * n.neurons * 2
         units += (act + idle) * 128
+        units_act += act * 128
     bytes_launch /= nl
     units /= nl
+    units_act /= nl
     kavg_ms = kms / max(kn, 1)
     pk = peaks()
     achieved = bytes_launch / (kavg_ms * 1e-3) / 1e9
@@ -535,7 +559,7 @@ def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), bat
                          "peak_source": pk["source"] + " (hbm_gbs, of measured copy bandwidth)",
                          "timing": "one CUDA event pair recorded by each timed graph replay around its tick launches",
                          "avg_launch_us": kavg_ms * 1e3, "bytes_per_launch": bytes_launch,
-                         "sample_core_units_per_launch": units},
+                         "sample_core_units_per_launch": units, "active_units_per_launch": units_act},
             "parity": par, "clocks": clk.summary(), "generation_seconds": gen_s, "create_tune_first_run_seconds": tune_s,
             "cpu_baseline": {"value": n_cfg / cpu_s, "unit": "configuration-samples/s", "cores": thr, "kind": "oracle",
                              "sample": f"one sample of each of the {n_cfg} configurations, {window} ticks "
@@ -595,6 +619,44 @@ def bench_xbar(ranc, torch, steps, warmup, batch=4096, p_active=0.2):
                        "equal": all(v["equal_to_oracle"] for v in res.values())}}
 
 
+def other_rows(ranc, torch, steps, warmup):
+    """Compact lines of the other measured rows, run after the headline with
+    the same step counts: the design sweep (64 configurations in one launch per
+    tick), the crossbar-product formulations, the TrueNorth-sized grid, the
+    streamed MNIST-512c run and the surrogate-ranked exploration.  A row that
+    fails is reported with its error instead of stopping the benchmark."""
+    rows = {}
+
+    def keep(name, fn, fields):
+        try:
+            t0 = time.perf_counter()
+            r = fn()
+            rows[name] = {k: r[k] for k in fields if k in r}
+            rows[name]["wall_seconds"] = time.perf_counter() - t0
+        except Exception as e:  # a failed extra row must not hide the headline
+            rows[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+
+    keep("f1_design_sweep", lambda: bench_sweep(ranc, torch, steps, warmup),
+         ("metric", "value", "unit", "ms_per_step", "config", "synaptic_events_per_sec", "launches_per_step",
+          "tuning", "roofline", "parity", "cpu_baseline", "dtype"))
+    keep("f4_crossbar_formulations", lambda: bench_xbar(ranc, torch, max(steps, 3), warmup),
+         ("metric", "unit", "config", "forms", "fastest", "parity"))
+    keep("f3_truenorth_ref", lambda: bench_truenorth(ranc, torch, steps, warmup),
+         ("metric", "value", "unit", "avg_tick_us", "paper_context", "cpu_baseline"))
+    keep("f3_stream", lambda: bench_stream(ranc, torch, steps, warmup),
+         ("metric", "value", "unit", "avg_tick_us", "output_events", "gpu_launches", "paper_context", "cpu_baseline"))
+
+    def dse_row():
+        from paper_2404_16208_gb300 import dse
+        return dse.explore(n_train=512, n_val=128, n_candidates=20000, top_k=64, seed=11, steps=2000, n_samples=256)
+    keep("f2_surrogate_dse", dse_row,
+         ("val_mae_agreement", "val_mae_rel_traffic", "val_spearman_objective", "top_true_objective_mean",
+          "random_true_objective_mean", "gain_mean", "spearman_top_pred_vs_true", "seconds_per_sim",
+          "train_seconds", "rank_seconds", "exact_sims_saved"))
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,6 +668,11 @@ def main():
                     help="samples per batched step (profiling runs use a smaller case)")
     ap.add_argument("--legs", default="batched,plain", help="comma list of legs to run (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-configs", type=int, default=64, help="sweep workload: configurations (profiling runs use fewer)")
+    ap.add_argument("--sweep-core-max", type=int, default=1024, help="sweep workload: largest core count")
+    ap.add_argument("--sweep-batch", type=int, default=1024, help="sweep workload: samples per configuration")
+    ap.add_argument("--no-other-rows", action="store_true",
+                    help="skip the compact lines of the other measured rows (sweep, formulations, TrueNorth, stream, DSE)")
     ap.add_argument("--workload", default="mnist512", choices=["mnist512", "truenorth", "dse", "stream", "sweep", "xbar"],
                     help="truenorth: the 64x64-core reference grid of Table I, 500 ticks, batch 1; "
                          "stream: Table I's streamed 10 010-tick MNIST-512c shape, one frame per tick; "
@@ -666,7 +733,8 @@ def main():
         return
     if args.workload == "sweep":
         if rank == 0:
-            line = bench_sweep(ranc, torch, args.steps, args.warmup)
+            line = bench_sweep(ranc, torch, args.steps, args.warmup, n_cfg=args.sweep_configs,
+                               core_range=(min(64, args.sweep_core_max), args.sweep_core_max), batch=args.sweep_batch)
             print(json.dumps(line))
             if not line["parity"]["equal"]:
                 sys.exit(1)
@@ -757,9 +825,11 @@ def main():
              "ms_per_step": ms_p / max(1, min(args.steps, 2)), "samples_per_step": npl, "batch": 1,
              "kernel": {"name": "plain_window_kernel (persistent, grid barrier per tick)", "avg_tick_us": ekp * 1e3,
                         "bound": "latency (state L2-resident at batch 1; grid barrier per tick)",
-                        "achieved_gbs": pbytes / (ekp * 1e-3) / 1e9, "l2_copy_gbs": l2_gbs,
-                        "frac_l2": pbytes / (ekp * 1e-3) / 1e9 / l2_gbs,
-                        "l2_peak_source": "measured in this run: torch copy of 2 x 16 MiB, L2-resident"}}
+                        "l2_bytes_per_tick": PLAIN_L2_BYTES_PER_TICK,
+                        "l2_gbs": PLAIN_L2_BYTES_PER_TICK / (ekp * 1e-3) / 1e9, "l2_copy_gbs": l2_gbs,
+                        "frac_l2": PLAIN_L2_BYTES_PER_TICK / (ekp * 1e-3) / 1e9 / l2_gbs,
+                        "l2_peak_source": "measured in this run: graph of 40 copies of 48 MiB, L2-resident",
+                        "per_tick_kernel_algorithmic_gbs": pbytes / (ekp * 1e-3) / 1e9}}
     e2e = e2e_batched(ranc, torch, net, x, nb)
 
     cpu, ref_out = None, None
@@ -797,6 +867,8 @@ def main():
         "clocks": clk.summary(), "gpu_launches": int(br["launches"]),
         "graph": {"captures": br["graph"][0], "replays": br["graph"][1]},
     }
+    if rank == 0 and ws == 1 and not args.no_other_rows:
+        line["other_rows"] = other_rows(ranc, torch, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     extern __shared__ __align__(16) uint32_t smp[];
     __shared__ uint32_t red[kMaxStepUnits][4];
     __shared__ int act_sh[kMaxStepUnits];
+    __shared__ int ub_sh[kMaxStepUnits], uc_sh[kMaxStepUnits];  // sample and core of each unit
     __shared__ int s_ok;
     const int N = a.N, AW = a.AW, SW = a.SW, C = a.C;
     const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
@@ -463,6 +464,13 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     auto unit = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };  // b * C + c
     unsigned gen = 0;
     if (tid == 0) s_ok = 1;
+    for (int i = tid; i < m; i += nt) {
+        ub_sh[i] = unit(i) / C;
+        uc_sh[i] = unit(i) % C;
+    }
+    // Phase C: thread tid updates neuron tid % N of units (round * upr + tid / N).
+    const int upr = nt / N, my_slot = tid / N, my_n = tid % N;
+    __syncthreads();
     for (int t = 0; t < n_ticks; ++t) {
         const long long tick = a.tick + t;
         const int r0 = (int)(tick & (kRows - 1));
@@ -471,18 +479,19 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
         for (int i = tid; i < m; i += nt) act_sh[i] = 0;
         __syncthreads();
         for (int i = tid; i < m * AW; i += nt) {
-            uint32_t *row = a.ring + ((size_t)unit(i / AW) * kRows + r0) * AW + i % AW;
+            const int k = i / AW;
+            uint32_t *row = a.ring + (((size_t)ub_sh[k] * C + uc_sh[k]) * kRows + r0) * AW + (i - k * AW);
             const uint32_t w = *row;
             sb[i] = w;
             if (w) {
                 *row = 0u;
-                act_sh[i / AW] = 1;
+                act_sh[k] = 1;
             }
         }
         __syncthreads();
         if (tick < a.in_ticks) {
             for (int i = 0; i < m; ++i) {
-                const int u = unit(i), b = u / C, c = u % C;
+                const int b = ub_sh[i], c = uc_sh[i];
                 if (b >= a.n_valid) continue;
                 const uint32_t *in = a.inputs + ((size_t)b * a.in_ticks + tick) * a.in_words;
                 for (int k = a.in_ptr[c] + tid; k < a.in_ptr[c + 1]; k += nt) {
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
         // ---- B: integration of the active units
         for (int i = 0; i < m; ++i) {
             if (!act_sh[i]) continue;  // uniform over the CTA
-            const int c = unit(i) % C;
+            const int c = uc_sh[i];
             for (int k = tid; k < SW * 32; k += nt) perm[k] = a.axperm[(size_t)c * SW * 32 + k];
             for (int k = tid; k < SW; k += nt) wt[k] = a.wtype[(size_t)c * SW + k];
             __syncthreads();
@@ -515,34 +524,33 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
             }
             __syncthreads();
         }
-        // ---- C: neuron updates of every unit, four per thread per round
-        for (int base = tid; base < m * N; base += 4 * nt) {
+        // ---- C: neuron updates of every unit: four units per thread per round,
+        // their loads issued first
+        for (int i0 = 0; i0 < m; i0 += 4 * upr) {
             int vv[4];
             int4 pr[4];
-            int *vp[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int idx = base + q * nt;
-                if (idx >= m * N) break;
-                const int i = idx / N, n = idx % N, u = unit(i), c = u % C;
-                vp[q] = a.V + (size_t)u * N + n;
-                vv[q] = *vp[q];
-                pr[q] = a.prm[(size_t)c * N + n];
+                const int i = i0 + q * upr + my_slot;
+                if (my_slot >= upr || i >= m) break;  // uniform per warp (N is a multiple of 32)
+                vv[q] = a.V[((size_t)ub_sh[i] * C + uc_sh[i]) * N + my_n];
+                pr[q] = a.prm[(size_t)uc_sh[i] * N + my_n];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int idx = base + q * nt;
-                if (idx >= m * N) break;  // uniform per warp (N is a multiple of 32)
-                const int i = idx / N, n = idx % N, u = unit(i), b = u / C, c = u % C;
+                const int i = i0 + q * upr + my_slot;
+                if (my_slot >= upr || i >= m) break;
+                const int b = ub_sh[i], c = uc_sh[i], n = my_n;
+                const size_t u = (size_t)b * C + c;
                 int v = vv[q] + (act_sh[i] ? dvs[i * N + n] : 0) + pr[q].x;
                 const bool fire = v >= pr[q].y;
                 if (fire)
                     v = pr[q].w;
                 else if (v < pr[q].z)
                     v = a.neg_mode ? pr[q].w : pr[q].z;
-                *vp[q] = v;
+                a.V[u * N + n] = v;
                 const unsigned fm = __ballot_sync(0xffffffffu, fire);
-                if (lane == 0) a.spk[(size_t)u * a.NW + n / 32] = fm;
+                if (lane == 0) a.spk[u * a.NW + n / 32] = fm;
                 uint32_t kind = 0u;
                 if (fire) {
                     const uint2 d = a.dst[(size_t)c * N + n];
@@ -568,8 +576,9 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
         }
         __syncthreads();
         for (int i = tid; i < m * 4; i += nt) {
-            const int u = unit(i / 4);
-            if (u / C < a.n_valid && red[i / 4][i % 4]) a.cnt[(size_t)u * 4 + i % 4] += red[i / 4][i % 4];
+            const int k = i >> 2;
+            if (ub_sh[k] < a.n_valid && red[k][i & 3])
+                a.cnt[((size_t)ub_sh[k] * C + uc_sh[k]) * 4 + (i & 3)] += red[k][i & 3];
         }
         // Failure-detection test: CTA 0 does not arrive at the first barrier.
         if (!grid_sync(bar, gridDim.x, gen, &s_ok, a.stall_test && blockIdx.x == 0 && t == 0)) {
