@@ -551,8 +551,9 @@ def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), bat
             "synaptic_events_per_sec": events / sec, "gpu_launches": int(launches),
             "launches_per_step": launches / steps, "tuning": {"chosen": {"weight_stages": tuning[0],
                                                                            "max_weight_stages": tuning[1],
-                                                                           "cost_mma": tuning[2],
-                                                                           "cost_slice": tuning[3]},
+                                                                           "cost_item": tuning[2],
+                                                                           "cost_mma": tuning[3],
+                                                                           "cost_slice": tuning[4]},
                                                                 "candidates_seconds": next(iter(sw.tuning.values()))["seconds"]},
             "roofline": {"kernel": "multi_tick_kernel", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                          "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,

@@ -157,16 +157,19 @@ int ranc_create_multi(const ranc_desc *const *descs, int32_t n_networks, int32_t
  * folded weights are copied into a ring of `weight_stages` 16 KB shared-memory
  * stages ahead of the MMAs (2 .. max_weight_stages, which the largest axon
  * count of the handle bounds).  The items of a tick are split over the CTAs by
- * a cost prefix: an item that receives spikes costs cost_mma per (K-block,
- * slice) plus cost_slice per slice, one that receives none cost_slice per
- * slice.  Results do not depend on these settings, only the time does.
+ * a cost prefix: an item that receives spikes costs cost_item, plus
+ * cost_slice per slice, plus cost_mma per (K-block, slice); one that receives
+ * none costs 2 * cost_slice per slice.  The defaults (4, 1, 3) fit the
+ * kernel's measured per-item, per-slice and per-MMA-group times.  Results
+ * do not depend on these settings, only the time does.
  * ranc_set_multi_tuning synchronises the handle's stream, and the next
  * ranc_run_samples call records its window graph again.  Errors:
  * RANC_EINVAL for settings out of range, RANC_ESTATE on a handle made by
  * ranc_create. */
-int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_mma, int32_t cost_slice);
-int ranc_get_multi_tuning(const ranc_sim *sim, int32_t *weight_stages, int32_t *max_weight_stages, int32_t *cost_mma,
-                          int32_t *cost_slice);
+int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_item, int32_t cost_mma,
+                          int32_t cost_slice);
+int ranc_get_multi_tuning(const ranc_sim *sim, int32_t *weight_stages, int32_t *max_weight_stages,
+                          int32_t *cost_item, int32_t *cost_mma, int32_t *cost_slice);
 
 /* Replace the input schedule with `bits` (host) [batch][n_ticks][ceil(n_inputs/32)]:
  * line i of input tick j is bit i%32 of word i/32 and is written into the

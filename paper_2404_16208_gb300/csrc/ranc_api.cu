@@ -671,16 +671,18 @@ extern "C" int ranc_create_multi(const ranc_desc *const *descs, int32_t n_networ
     return RANC_OK;
 }
 
-extern "C" int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_mma, int32_t cost_slice) {
+extern "C" int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32_t cost_item, int32_t cost_mma,
+                                     int32_t cost_slice) {
     CHECK_LIVE(sim);
     if (!sim->multi) return fail(sim, RANC_ESTATE, "the pipeline tuning belongs to multi-network handles");
-    int st = 0, mx = 0, cm = 0, cs = 0;
-    multi_get_tuning(sim, &st, &mx, &cm, &cs);
+    int st = 0, mx = 0, ci = 0, cm = 0, cs = 0;
+    multi_get_tuning(sim, &st, &mx, &ci, &cm, &cs);
     if (weight_stages < 2 || weight_stages > mx)
         return fail(sim, RANC_EINVAL, "weight stages must be in [2, %d] for this handle (got %d)", mx, weight_stages);
-    if (cost_mma < 0 || cost_slice < 1 || cost_mma > 1024 || cost_slice > 1024)
-        return fail(sim, RANC_EINVAL, "split costs must satisfy 0 <= cost_mma <= 1024 and 1 <= cost_slice <= 1024");
-    CUDA_OR_FAIL(sim, multi_set_tuning(sim, weight_stages, cost_mma, cost_slice));
+    if (cost_item < 0 || cost_mma < 0 || cost_slice < 1 || cost_item > 1024 || cost_mma > 1024 || cost_slice > 1024)
+        return fail(sim, RANC_EINVAL,
+                    "split costs must satisfy 0 <= cost_item <= 1024, 0 <= cost_mma <= 1024 and 1 <= cost_slice <= 1024");
+    CUDA_OR_FAIL(sim, multi_set_tuning(sim, weight_stages, cost_item, cost_mma, cost_slice));
     if (sim->win_exec) {  // a recorded window graph holds the old launch arguments
         cudaGraphExecDestroy(sim->win_exec);
         sim->win_exec = nullptr;
@@ -689,13 +691,14 @@ extern "C" int ranc_set_multi_tuning(ranc_sim *sim, int32_t weight_stages, int32
 }
 
 extern "C" int ranc_get_multi_tuning(const ranc_sim *sim, int32_t *weight_stages, int32_t *max_weight_stages,
-                                     int32_t *cost_mma, int32_t *cost_slice) {
-    if (!sim || !weight_stages || !max_weight_stages || !cost_mma || !cost_slice) return RANC_EINVAL;
+                                     int32_t *cost_item, int32_t *cost_mma, int32_t *cost_slice) {
+    if (!sim || !weight_stages || !max_weight_stages || !cost_item || !cost_mma || !cost_slice) return RANC_EINVAL;
     if (!sim->multi) return RANC_ESTATE;
-    int st = 0, mx = 0, cm = 0, cs = 0;
-    multi_get_tuning(sim, &st, &mx, &cm, &cs);
+    int st = 0, mx = 0, ci = 0, cm = 0, cs = 0;
+    multi_get_tuning(sim, &st, &mx, &ci, &cm, &cs);
     *weight_stages = st;
     *max_weight_stages = mx;
+    *cost_item = ci;
     *cost_mma = cm;
     *cost_slice = cs;
     return RANC_OK;

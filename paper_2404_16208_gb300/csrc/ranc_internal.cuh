@@ -232,7 +232,7 @@ int multi_networks(const ranc_sim *sim);
 cudaError_t multi_reserve_inputs(ranc_sim *sim, int n_ticks, const void **buffer);
 cudaError_t launch_multi_inputs(ranc_sim *sim, const uint32_t *dev_bits, int n_samples, int n_ticks);
 cudaError_t launch_multi_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t *spk);
-void multi_get_tuning(const ranc_sim *sim, int *stages, int *max_stages, int *cost_mma, int *cost_slice);
-cudaError_t multi_set_tuning(ranc_sim *sim, int stages, int cost_mma, int cost_slice);
+void multi_get_tuning(const ranc_sim *sim, int *stages, int *max_stages, int *cost_item, int *cost_mma, int *cost_slice);
+cudaError_t multi_set_tuning(ranc_sim *sim, int stages, int cost_item, int cost_mma, int cost_slice);
 void multi_teardown(ranc_sim *sim);
 }  // namespace ranc

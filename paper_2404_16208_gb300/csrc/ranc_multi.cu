@@ -296,37 +296,107 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
         const int q = warp & 3, cc = warp >> 2;
         constexpr int kVecs = 32 * (int)sizeof(VT) / 16;
         constexpr bool kHalf = std::is_same<VT, __half>::value;
-        const int wt = warp * 32 + lane;  // build task index base (0..511)
+        // With 2-byte potentials the loads of the epilogue's first slice are
+        // issued before the build (their registers fit beside the build's).
+        constexpr bool kPre0 = sizeof(VT) == 2;
+        const int wt = warp * 32 + lane;  // build task index base: tasks wt and wt + 512 (2A <= 1024)
         int nb = 0;                       // operands built (phases of s_full / s_free)
         int ns = 0;                       // accumulator slices consumed (ring position)
         bool stop = false;
+        // Words of the next active item's operand, loaded one build ahead (row
+        // r0 receives no delivery in this tick: every delay is at least 1), and
+        // the fan-in range, first input line and out-degree of each task's
+        // axon, kept while the core does not change.
+        int fg = -1, f0[2] = {0, 0}, f1[2] = {0, 0}, ln0[2] = {0, 0};
+        uint32_t odr[2] = {0u, 0u};
+        uint2 wr[2], wi[2];
+        auto load_words = [&](int li) {
+            const int it = i0 + li, g = it / T, j = it - g * T;
+            const SegDev sd = a.seg[a.core_seg[g]];
+            const int c = g - sd.core0;
+            const uint2 *row = reinterpret_cast<const uint2 *>(a.ring + sd.roff + (((size_t)j * sd.C + c) * kRows + r0) * sd.A * 4);
+            const bool newc = g != fg;
+            fg = g;
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int tau = wt + t * kWorkersM * 32, rax = tau >> 1, rhf = tau & 1;
+                wr[t] = wi[t] = make_uint2(0u, 0u);
+                if (tau >= 2 * sd.A) continue;
+                wr[t] = row[rax * 2 + rhf];
+                if (newc) {
+                    odr[t] = a.outdeg[sd.aoff + (size_t)c * sd.A + rax];
+                    if (inputs) {
+                        const int *fp = a.fin_ptr + sd.foff + (size_t)c * (sd.A + 1) + rax;
+                        f0[t] = fp[0];
+                        f1[t] = fp[1];
+                        ln0[t] = f1[t] > f0[t] ? a.fin_line[f0[t]] : 0;
+                    }
+                }
+                if (inputs && f1[t] > f0[t]) {
+                    const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
+                    wi[t] = in[(size_t)ln0[t] * 2];
+                    for (int e = f0[t] + 1; e < f1[t]; ++e) {  // further lines (each waits for its load)
+                        const uint2 y = in[(size_t)a.fin_line[e] * 2];
+                        wi[t].x |= y.x;
+                        wi[t].y |= y.y;
+                    }
+                }
+            }
+        };
+        auto next_active = [&](int li) {
+            while (li < n_items && !active_at(li)) ++li;
+            return li;
+        };
+        int kn = next_active(0);  // next item to build
+        if (kn < n_items) load_words(kn);
+        // One slice of the epilogue item as this lane sees it: parameters,
+        // destination and 32 potentials of neuron h*128 + 32q + lane.
+        struct Slice {
+            int4 pr;
+            uint2 dd;
+            uint4 vb[kVecs];
+        };
+        auto load_slice = [&](const SegDev &sd, int ce, int je, int h, Slice &L) {
+            const int n = h * 128 + q * 32 + lane;
+            const size_t pn = (size_t)sd.poff + (size_t)ce * sd.N + n;
+            L.pr = a.prm[pn];
+            L.dd = a.dst[pn];
+            if (a.v0_now) {
+                const uint4 vz = v_splat<VT>(a.v0[pn]);
+#pragma unroll
+                for (int e = 0; e < kVecs; ++e) L.vb[e] = vz;
+            } else {
+                const uint4 *vp = reinterpret_cast<const uint4 *>(reinterpret_cast<const VT *>(a.V) + sd.voff +
+                                                                  v_index<VT>(je, ce, cc, n & ~31, 0, sd.C, sd.N)) + lane;
+#pragma unroll
+                for (int e = 0; e < kVecs; ++e) L.vb[e] = vp[e * 32];
+            }
+        };
         for (int k = 0; k <= n_items && !stop; ++k) {
             if (warp == 0 && lane == 0) cur_sh = k;
+            // ---- (0) slice 0 of the epilogue item k - 1: loads in flight during the build
+            const int le = k - 1, ite = i0 + le, ge = ite / T, je = ite - ge * T;
+            const SegDev sde = a.seg[a.core_seg[k > 0 ? ge : 0]];
+            const int ce = ge - sde.core0;
+            Slice cur;
+            if (kPre0 && k > 0) load_slice(sde, ce, je, 0, cur);
             // ---- (1) build the operand of item k
-            if (k < n_items && active_at(k)) {
+            if (k < n_items && k == kn) {
                 const int it = i0 + k, g = it / T, j = it - g * T;
                 const SegDev sd = a.seg[a.core_seg[g]];
                 const int c = g - sd.core0;
                 if (!wait(&s_free, (nb & 1) ^ 1)) break;
                 uint32_t ev = 0u;
                 uint2 *row = reinterpret_cast<uint2 *>(a.ring + sd.roff + (((size_t)j * sd.C + c) * kRows + r0) * sd.A * 4);
-                for (int tau = wt; tau < 2 * sd.A; tau += kWorkersM * 32) {
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int tau = wt + t * kWorkersM * 32;
+                    if (tau >= 2 * sd.A) continue;
                     const int rax = tau >> 1, rhf = tau & 1;
-                    uint2 w = row[rax * 2 + rhf];
-                    if (w.x | w.y) row[rax * 2 + rhf] = make_uint2(0u, 0u);
-                    if (inputs) {
-                        const int *fp = a.fin_ptr + sd.foff + (size_t)c * (sd.A + 1) + rax;
-                        const int f0 = fp[0], f1 = fp[1];
-                        const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
-                        for (int e = f0; e < f1; ++e) {
-                            const uint2 y = in[(size_t)a.fin_line[e] * 2];
-                            w.x |= y.x;
-                            w.y |= y.y;
-                        }
-                    }
+                    if (wr[t].x | wr[t].y) row[rax * 2 + rhf] = make_uint2(0u, 0u);
+                    const uint2 w = make_uint2(wr[t].x | wi[t].x, wr[t].y | wi[t].y);
                     const int m0 = j * 128 + rhf * 64;
-                    ev += a.outdeg[sd.aoff + (size_t)c * sd.A + rax] *
-                          (uint32_t)(__popc(w.x & valid_mask(a.n_valid, m0)) + __popc(w.y & valid_mask(a.n_valid, m0 + 32)));
+                    ev += odr[t] * (uint32_t)(__popc(w.x & valid_mask(a.n_valid, m0)) + __popc(w.y & valid_mask(a.n_valid, m0 + 32)));
                     // Row rax of the 64-sample half rhf (128-byte swizzle; the
                     // two halves write their chunks in opposite order).
                     const int r8 = rax & 7;
@@ -343,33 +413,23 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_full);
                 ++nb;
+                kn = next_active(k + 1);
+                if (kn < n_items) load_words(kn);
                 ev = __reduce_add_sync(0xffffffffu, ev);
                 if (lane == 0 && ev) atomicAdd(a.cnt + ((size_t)j * a.C + g) * 4 + 3, (unsigned long long)ev);
             }
             // ---- (2) epilogue of item k - 1
             if (k == 0) continue;
-            const int le = k - 1, ite = i0 + le, ge = ite / T, je = ite - ge * T;
             const bool act = active_at(le);
-            const SegDev sd = a.seg[a.core_seg[ge]];
-            const int ce = ge - sd.core0;
-            VT *Vg = reinterpret_cast<VT *>(a.V) + sd.voff;
+            VT *Vg = reinterpret_cast<VT *>(a.V) + sde.voff;
             const uint32_t valid = valid_mask(a.n_valid, je * 128 + cc * 32);
             uint32_t n_sp = 0, n_pk = 0, n_out = 0;
-            for (int h = 0; h < sd.NH; ++h) {
+            for (int h = 0; h < sde.NH; ++h) {
+                if (!kPre0 || h > 0) load_slice(sde, ce, je, h, cur);
                 const int n = h * 128 + q * 32 + lane;
-                const size_t pn = (size_t)sd.poff + (size_t)ce * sd.N + n;
-                const int4 pr = a.prm[pn];
-                const uint2 dd = a.dst[pn];
-                uint4 *vp = reinterpret_cast<uint4 *>(Vg + v_index<VT>(je, ce, cc, n & ~31, 0, sd.C, sd.N)) + lane;
-                uint4 vb[kVecs];
-                if (a.v0_now) {
-                    const uint4 vz = v_splat<VT>(a.v0[pn]);
-#pragma unroll
-                    for (int e = 0; e < kVecs; ++e) vb[e] = vz;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < kVecs; ++e) vb[e] = vp[e * 32];
-                }
+                const int4 pr = cur.pr;
+                const uint2 dd = cur.dd;
+                uint4 *vp = reinterpret_cast<uint4 *>(Vg + v_index<VT>(je, ce, cc, n & ~31, 0, sde.C, sde.N)) + lane;
                 const int slot = ns & (kSlots - 1);
                 if (act) {
                     if (!wait(&acc_full[slot], (ns / kSlots) & 1)) {
@@ -399,7 +459,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                         uint32_t wv[8];
 #pragma unroll
                         for (int q2 = 0; q2 < 2; ++q2) {
-                            const uint4 u = vb[hf * 2 + q2];
+                            const uint4 u = cur.vb[hf * 2 + q2];
                             wv[4 * q2] = u.x;
                             wv[4 * q2 + 1] = u.y;
                             wv[4 * q2 + 2] = u.z;
@@ -428,7 +488,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                         // (wrap-around arithmetic, exact when V + dV + leak fits int32).
                         const uint32_t lam = (uint32_t)pr.x - 0x4B400000u;
                         int v[16];
-                        unpack16<VT>(vb, hf, v);
+                        unpack16<VT>(cur.vb, hf, v);
 #pragma unroll
                         for (int i = 0; i < 16; ++i) {
                             const int x = (int)((uint32_t)v[i] + (uint32_t)f32_bits_minus_bias(d[i]) + lam);
@@ -446,7 +506,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                     if (lane == 0) mbar_arrive(&acc_empty[slot]);
                     ++ns;
                 }
-                a.spk[sd.soff + (((size_t)je * sd.C + ce) * 4 + cc) * sd.N + n] = mask;
+                a.spk[sde.soff + (((size_t)je * sde.C + ce) * 4 + cc) * sde.N + n] = mask;
                 const uint32_t live = mask & valid;
                 const uint32_t kind = dest_kind(dd);
                 n_sp += __popc(live);
@@ -454,8 +514,8 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                     n_pk += __popc(live);
                     const uint32_t ax = dest_axon(dd);
                     const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
-                    atomicOr(a.ring + sd.roff + ((((size_t)je * sd.C + dd.x) * kRows + r) * sd.A + ax) * 4 + cc, mask);
-                    a.stamp[(size_t)r * a.spitch + (size_t)(sd.core0 + dd.x) * T + je] =
+                    atomicOr(a.ring + sde.roff + ((((size_t)je * sde.C + dd.x) * kRows + r) * sde.A + ax) * 4 + cc, mask);
+                    a.stamp[(size_t)r * a.spitch + (size_t)(sde.core0 + dd.x) * T + je] =
                         (uint8_t)((a.sclock + dest_delay(dd)) >> 4);
                 }
                 // Output bus: one warp-wide pass per output neuron that fired.
@@ -622,7 +682,14 @@ __global__ void export_multi(const SegDev *seg, int n_seg, const VT *V, const ui
 
 struct Multi {
     int n_seg = 0, kbmax = 0, stages = 4, n_sm = 0, Lpad = 0;
-    int cost_mma = 1, cost_slice = 4;  // split cost of an item: cost_mma per (K-block, slice) MMA group + cost_slice per slice
+    // Split cost of an item that receives spikes: cost_item + cost_slice per
+    // slice + cost_mma per (K-block, slice) MMA group; of one that receives
+    // none: 2 * cost_slice per slice.  The defaults are a least-squares fit of
+    // per-CTA busy times against the CTAs' item mix on a 64-network sweep
+    // (units of about 0.4 us: 1.55 us per item, 1.2 us per slice, 0.4 us per
+    // MMA group; 2.5 us per slice of an idle item, whose potential loads find
+    // no operand build to hide behind).
+    int cost_item = 4, cost_mma = 1, cost_slice = 3;
     size_t smem = 0;
     std::vector<SegDev> seg;          // host copy of the network table
     SegDev *seg_dev = nullptr;
@@ -635,6 +702,12 @@ struct Multi {
     long long spitch = 0, ring_words = 0, v_elems = 0, spk_words = 0;
     std::vector<int> max_delay;       // per network: largest core-to-core delay
 };
+
+// Split costs of network sd's items (int32: at most 1024 + 1024 * 8 * 4 + 1024 * 4 per item).
+void set_costs(SegDev &sd, const Multi &m) {
+    sd.cost_act = std::max(1, m.cost_item + m.cost_mma * sd.KB * sd.NH + m.cost_slice * sd.NH);
+    sd.cost_idle = std::max(1, 2 * m.cost_slice * sd.NH);
+}
 
 Multi *M_of(ranc_sim *s) { return static_cast<Multi *>(s->multi); }
 
@@ -699,10 +772,7 @@ cudaError_t multi_setup(ranc_sim *sim, const ranc_desc *const *descs, int n, std
         sd.C = C; sd.A = A; sd.N = N; sd.NH = N / 128; sd.KB = A / 64; sd.core0 = C_total;
         sd.voff = vsz_elems; sd.roff = ring_w; sd.soff = spk_w; sd.poff = P; sd.woff = wblocks; sd.foff = fptr_n;
         sd.aoff = aout_n;
-        // Split costs: an active item's MMAs grow with (A / 64) * (N / 128),
-        // its epilogue with N / 128; an idle one has only the epilogue.
-        sd.cost_act = m->cost_mma * sd.KB * sd.NH + m->cost_slice * sd.NH;
-        sd.cost_idle = std::max(1, m->cost_slice * sd.NH);
+        set_costs(sd, *m);
         C_total += C;
         vsz_elems += (long long)T * C * 4 * N * 32;
         ring_w += (long long)T * C * kRows * A * 4;
@@ -955,23 +1025,22 @@ cudaError_t launch_multi_export(ranc_sim *sim, int b0, int nb, int *v, uint32_t 
     return cudaGetLastError();
 }
 
-void multi_get_tuning(const ranc_sim *sim, int *stages, int *max_stages, int *cost_mma, int *cost_slice) {
+void multi_get_tuning(const ranc_sim *sim, int *stages, int *max_stages, int *cost_item, int *cost_mma, int *cost_slice) {
     const Multi *m = static_cast<const Multi *>(sim->multi);
     *stages = m->stages;
     *max_stages = multi_max_stages(m->kbmax);
+    *cost_item = m->cost_item;
     *cost_mma = m->cost_mma;
     *cost_slice = m->cost_slice;
 }
 
-cudaError_t multi_set_tuning(ranc_sim *sim, int stages, int cost_mma, int cost_slice) {
+cudaError_t multi_set_tuning(ranc_sim *sim, int stages, int cost_item, int cost_mma, int cost_slice) {
     Multi *m = M_of(sim);
     m->stages = stages;
+    m->cost_item = cost_item;
     m->cost_mma = cost_mma;
     m->cost_slice = cost_slice;
-    for (SegDev &sd : m->seg) {
-        sd.cost_act = cost_mma * sd.KB * sd.NH + cost_slice * sd.NH;
-        sd.cost_idle = std::max(1, cost_slice * sd.NH);
-    }
+    for (SegDev &sd : m->seg) set_costs(sd, *m);
     cudaError_t e = cudaMemcpyAsync(m->seg_dev, m->seg.data(), sizeof(SegDev) * m->n_seg, cudaMemcpyHostToDevice, sim->stream);
     return e != cudaSuccess ? e : cudaStreamSynchronize(sim->stream);
 }

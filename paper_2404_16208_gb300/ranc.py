@@ -59,8 +59,8 @@ def load_library(path=LIB_PATH):
     sig = {
         "ranc_create": ([C.POINTER(ranc_desc), i32, i32, vp, C.POINTER(vp)], C.c_int),
         "ranc_create_multi": ([C.POINTER(C.POINTER(ranc_desc)), i32, i32, vp, C.POINTER(vp)], C.c_int),
-        "ranc_set_multi_tuning": ([vp, i32, i32, i32], C.c_int),
-        "ranc_get_multi_tuning": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
+        "ranc_set_multi_tuning": ([vp, i32, i32, i32, i32], C.c_int),
+        "ranc_get_multi_tuning": ([vp] + [C.POINTER(i32)] * 5, C.c_int),
         "ranc_load_inputs": ([vp, u32p, i32], C.c_int),
         "ranc_load_inputs_device": ([vp, vp, i32], C.c_int),
         "ranc_step": ([vp, i32], C.c_int),
@@ -157,13 +157,13 @@ def ranc_create_multi(nets, batch, stream=0):
     return h
 
 
-def ranc_set_multi_tuning(h, weight_stages, cost_mma, cost_slice):
-    _check(_lib.ranc_set_multi_tuning(h, int(weight_stages), int(cost_mma), int(cost_slice)), h)
+def ranc_set_multi_tuning(h, weight_stages, cost_item, cost_mma, cost_slice):
+    _check(_lib.ranc_set_multi_tuning(h, int(weight_stages), int(cost_item), int(cost_mma), int(cost_slice)), h)
 
 
 def ranc_get_multi_tuning(h):
-    """(weight_stages, max_weight_stages, cost_mma, cost_slice) of a multi-network handle."""
-    v = [C.c_int32() for _ in range(4)]
+    """(weight_stages, max_weight_stages, cost_item, cost_mma, cost_slice) of a multi-network handle."""
+    v = [C.c_int32() for _ in range(5)]
     _check(_lib.ranc_get_multi_tuning(h, *[C.byref(x) for x in v]), h)
     return tuple(x.value for x in v)
 
@@ -485,8 +485,8 @@ class MultiSim:
         """[n_networks, 2] active and idle item-ticks of each network."""
         return np.array([ranc_network_item_classes(self.h, k) for k in range(len(self.nets))], np.int64)
 
-    def set_tuning(self, weight_stages, cost_mma, cost_slice):
-        ranc_set_multi_tuning(self.h, weight_stages, cost_mma, cost_slice)
+    def set_tuning(self, weight_stages, cost_item, cost_mma, cost_slice):
+        ranc_set_multi_tuning(self.h, weight_stages, cost_item, cost_mma, cost_slice)
 
     def close(self):
         if self.h is not None:

@@ -187,8 +187,10 @@ class _MultiGroup:
         self.sims = []
 
 
-# Split cost settings (cost_mma, cost_slice) the tuner tries beside every weight-stage depth.
-COST_CANDIDATES = ((1, 4), (1, 2), (2, 4), (1, 8))
+# Split cost settings (cost_item, cost_mma, cost_slice) the tuner tries beside
+# every weight-stage depth: the library's default (a fit of the kernel's
+# measured per-item, per-slice and per-MMA-group times) and three neighbours.
+COST_CANDIDATES = ((4, 1, 3), (2, 1, 3), (6, 1, 3), (4, 1, 2))
 
 
 class Sweep:
@@ -220,7 +222,7 @@ class Sweep:
         cores = sum(self.nets[i].n_cores for i in members)
         if key[0] == "multi":
             shapes = sorted({(self.nets[i].axons, self.nets[i].neurons) for i in members})
-            return f"multi-neg{key[1]}-nets{len(members)}-cores{cores}-shapes{shapes}-b{self.batch}"
+            return f"multi-neg{key[1]}-nets{len(members)}-cores{cores}-shapes{shapes}-b{self.batch}-costs3"
         return f"path{key[0]}-A{key[1]}-N{key[2]}-neg{key[3]}-fmt{key[4]}-nets{len(members)}-cores{cores}-b{self.batch}"
 
     def _load_cache(self):
@@ -232,15 +234,15 @@ class Sweep:
     def _tune_multi(self, g, xp, window):
         """Times every (weight stages, split costs) candidate on the probe
         samples (one warm-up run each) and sets the fastest."""
-        _, mx, _, _ = g.sim.tuning()
+        mx = g.sim.tuning()[1]
         times = {}
         for stages in range(2, mx + 1):
-            for cm, cs in COST_CANDIDATES:
-                g.sim.set_tuning(stages, cm, cs)
+            for costs in COST_CANDIDATES:
+                g.sim.set_tuning(stages, *costs)
                 g.run(self.nets, xp, window)
                 t0 = time.perf_counter()
                 g.run(self.nets, xp, window)
-                times[f"{stages},{cm},{cs}"] = time.perf_counter() - t0
+                times[",".join(str(v) for v in (stages,) + tuple(costs))] = time.perf_counter() - t0
         best = min(times, key=times.get)
         return [int(v) for v in best.split(",")], times
 

@@ -104,24 +104,26 @@ def test_window_graph_tuning_and_full_state_read(ranc, oracle_mod):
     sim = ranc.MultiSim(nets, 128)
     dx = torch.from_numpy(x.view(np.int32)).cuda()
     dout = torch.zeros((S, sim.n_outputs), dtype=torch.int32, device="cuda")
-    st0, mx, cm0, cs0 = sim.tuning()
-    assert 2 <= st0 <= mx and mx >= 4
+    st0, mx, ci0, cm0, cs0 = sim.tuning()
+    assert 2 <= st0 <= mx and mx >= 4 and (ci0, cm0, cs0) == (4, 1, 3)
     settings = 0
     for stages in range(2, mx + 1):
-        for cm, cs in ((1, 4), (3, 1)):
-            sim.set_tuning(stages, cm, cs)  # the next call records the window graph again
-            assert sim.tuning() == (stages, mx, cm, cs)
+        for ci, cm, cs in ((4, 1, 3), (0, 3, 1)):
+            sim.set_tuning(stages, ci, cm, cs)  # the next call records the window graph again
+            assert sim.tuning() == (stages, mx, ci, cm, cs)
             for call in range(2):
                 dout.zero_()
                 ranc.ranc_run_samples(sim.h, dx.data_ptr(), S, t_in, window, dout.data_ptr(), ranc.RANC_MEM_DEVICE)
                 outs = sim.split_outputs(dout.cpu().numpy().view(np.uint32))
                 for k, (o, ref) in enumerate(zip(outs, refs)):
                     np.testing.assert_array_equal(o, ref["out"],
-                                                  err_msg=f"stages {stages}, costs {cm}/{cs}, call {call}, network {k}")
+                                                  err_msg=f"stages {stages}, costs {ci}/{cm}/{cs}, call {call}, network {k}")
             settings += 1
     assert ranc.ranc_graph_stats(sim.h) == (settings, settings)
     with pytest.raises(ranc.RancError):
-        sim.set_tuning(mx + 1, 1, 4)
+        sim.set_tuning(mx + 1, 4, 1, 3)
+    with pytest.raises(ranc.RancError):
+        sim.set_tuning(2, -1, 1, 3)
     # the last group's state after the window, every sample of the batch, with the digest
     last = oracle_runs(oracle_mod, nets, x[256:], window, trace=False)
     P = int(sim.poff[-1])
@@ -155,7 +157,7 @@ def test_unsupported_calls_and_shape_checks(ranc):
         ranc.MultiSim([nets[0], other], 64)
     plain = ranc.Sim(nets[0], 1, ranc.RANC_PATH_PLAIN)
     with pytest.raises(ranc.RancError) as ei:
-        ranc.ranc_set_multi_tuning(plain.h, 3, 1, 4)
+        ranc.ranc_set_multi_tuning(plain.h, 3, 4, 1, 3)
     assert ei.value.code == ranc.RANC_ESTATE
     plain.close()
 

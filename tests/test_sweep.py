@@ -126,8 +126,8 @@ def test_autotuned_sweep_caches_its_choice(oracle_mod, S, tmp_path):
             np.testing.assert_array_equal(cnt[k], r["counters"][:, :4].sum(0), err_msg=f"net {k}")
         assert [p[1] for p in sw.plans()] == ["multi"] and sw.multi_handle() is not None
         (sig, t), = sw.tuning.items()
-        stages, cm, cs = t["choice"]
-        assert sw.multi_handle().tuning() == (stages, sw.multi_handle().tuning()[1], cm, cs)
+        stages, ci, cm, cs = t["choice"]
+        assert sw.multi_handle().tuning() == (stages, sw.multi_handle().tuning()[1], ci, cm, cs)
         max_stages = sw.multi_handle().tuning()[1]
         assert len(t["seconds"]) == (max_stages - 1) * len(S.COST_CANDIDATES)  # every candidate was timed
         if round_ == 1:
