@@ -130,24 +130,33 @@ struct MultiArgs {
 // path, without deferred items): CTA b takes the items whose exclusive prefix
 // P satisfies b * W <= P * G < (b + 1) * W.  Run by all threads; on return
 // cut_sh holds [i0, i1) and, when the range fits kClsCapM, cls_sm the class of
-// each item of the range (2 active, 1 idle).
+// each item of the range (2 active, 1 idle).  The prefix is formed per core
+// (its T items share the network and the input flag; an input-driven core has
+// all of them active), each thread over a contiguous run of cores; only the
+// cores that hold a cut are walked item by item.  seg_sh (2 * n_seg counters)
+// collects the per-network item counts of the CTA's range.
 __device__ __noinline__ void split_multi(const MultiArgs &a, const int *cost_sh, long long *wsum_sh, int *cut_sh,
-                                         uint8_t *cls_sm) {
+                                         uint8_t *cls_sm, unsigned *seg_sh) {
     const uint8_t *const stamp_row = a.stamp_row, *const core_flags = a.core_flags, *const core_seg = a.core_seg;
-    const int items = a.items, T = a.T;
+    const int C = a.C, T = a.T, n_seg = a.n_seg;
     const bool all_active = a.all_active != 0, inputs = a.tick < (long long)a.in_ticks;
     const uint8_t cycle = (uint8_t)(a.sclock >> 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int per = (items + kThreadsM - 1) / kThreadsM;
-    const int t0 = min(items, tid * per), t1 = min(items, t0 + per);
-    auto cls_of = [&](int it, int g) -> int {
-        return (all_active || stamp_row[it] == cycle || (inputs && (core_flags[g] & 1))) ? 2 : 1;
+    for (int i = tid; i < 2 * n_seg; i += kThreadsM) seg_sh[i] = 0u;
+    const int per = (C + kThreadsM - 1) / kThreadsM;
+    const int g0 = min(C, tid * per), g1 = min(C, g0 + per);
+    auto all_of = [&](int g) -> bool { return all_active || (inputs && (core_flags[g] & 1)); };
+    auto n_active = [&](int g) -> int {  // active items of core g
+        if (all_of(g)) return T;
+        const uint8_t *st = stamp_row + (size_t)g * T;
+        int n = 0;
+        for (int j = 0; j < T; ++j) n += st[j] == cycle;
+        return n;
     };
-    auto cost_of = [&](int cls, int g) -> int { return cost_sh[2 * core_seg[g] + (cls == 2 ? 0 : 1)]; };
     long long csum = 0;
-    for (int it = t0; it < t1; ++it) {
-        const int g = it / T;
-        csum += cost_of(cls_of(it, g), g);
+    for (int g = g0; g < g1; ++g) {
+        const int s = core_seg[g], na = n_active(g);
+        csum += (long long)na * cost_sh[2 * s] + (long long)(T - na) * cost_sh[2 * s + 1];
     }
     long long cinc = csum;
 #pragma unroll
@@ -168,11 +177,26 @@ __device__ __noinline__ void split_multi(const MultiArgs &a, const int *cost_sh,
         const long long G = gridDim.x;
         const long long lo = ((long long)blockIdx.x * W + G - 1) / G, hi = ((long long)(blockIdx.x + 1) * W + G - 1) / G;
         int n0 = 0, n1 = 0;
-        for (int it = t0; it < t1; ++it) {
-            n0 += P < lo;
-            n1 += P < hi;
-            const int g = it / T;
-            P += cost_of(cls_of(it, g), g);
+        for (int g = g0; g < g1; ++g) {
+            const int s = core_seg[g];
+            const int ca = cost_sh[2 * s], ci = cost_sh[2 * s + 1];
+            const bool all = all_of(g);
+            const int na = all ? T : n_active(g);
+            const long long cc = (long long)na * ca + (long long)(T - na) * ci;
+            // items of this core whose exclusive prefix lies below lo / hi
+            for (int b = 0; b < 2; ++b) {
+                const long long lim = b ? hi : lo;
+                int n = 0;
+                if (P + cc <= lim) {
+                    n = T;
+                } else if (P < lim) {
+                    long long Pj = P;
+                    const uint8_t *st = stamp_row + (size_t)g * T;
+                    for (int j = 0; j < T && Pj < lim; ++j, ++n) Pj += (all || st[j] == cycle) ? ca : ci;
+                }
+                (b ? n1 : n0) += n;
+            }
+            P += cc;
         }
         n0 = __reduce_add_sync(0xffffffffu, n0);
         n1 = __reduce_add_sync(0xffffffffu, n1);
@@ -182,33 +206,27 @@ __device__ __noinline__ void split_multi(const MultiArgs &a, const int *cost_sh,
         }
     }
     __syncthreads();
-    const int i0 = cut_sh[0], i1 = cut_sh[1];
+    const int i0 = cut_sh[0], i1 = cut_sh[1], n_items = i1 - i0;
     int n_up = 0, n_act = 0;
-    int sg = -1, s_up = 0, s_act = 0;  // per-network counts of the current run of items
-    auto flush = [&]() {
-        if (sg >= 0 && s_up) {
-            atomicAdd(a.item_ticks + 3 + 2 * sg, (unsigned long long)s_up);
-            if (s_act) atomicAdd(a.item_ticks + 4 + 2 * sg, (unsigned long long)s_act);
-        }
-        s_up = s_act = 0;
-    };
-    for (int it = max(t0, i0); it < min(t1, i1); ++it) {
-        const int g = it / T, cls = cls_of(it, g);
-        if (i1 - i0 <= kClsCapM) cls_sm[it - i0] = (uint8_t)cls;
+    for (int li = tid; li < n_items; li += kThreadsM) {
+        const int it = i0 + li, g = it / T;
+        const bool act = all_of(g) || stamp_row[it] == cycle;
+        if (n_items <= kClsCapM) cls_sm[li] = act ? 2 : 1;
+        const int s = core_seg[g];
+        atomicAdd(&seg_sh[2 * s], 1u);
+        if (act) atomicAdd(&seg_sh[2 * s + 1], 1u);
         ++n_up;
-        n_act += cls == 2;
-        if (core_seg[g] != sg) {
-            flush();
-            sg = core_seg[g];
-        }
-        ++s_up;
-        s_act += cls == 2;
+        n_act += act;
     }
-    flush();
     n_up = __reduce_add_sync(0xffffffffu, n_up);
     n_act = __reduce_add_sync(0xffffffffu, n_act);
     if (lane == 0 && n_up) atomicAdd(a.item_ticks, (unsigned long long)n_up);
     if (lane == 0 && n_act) atomicAdd(a.item_ticks + 2, (unsigned long long)n_act);
+    __syncthreads();
+    for (int s = tid; s < n_seg; s += kThreadsM) {
+        if (seg_sh[2 * s]) atomicAdd(a.item_ticks + 3 + 2 * s, (unsigned long long)seg_sh[2 * s]);
+        if (seg_sh[2 * s + 1]) atomicAdd(a.item_ticks + 4 + 2 * s, (unsigned long long)seg_sh[2 * s + 1]);
+    }
 }
 
 template <typename VT, int kNegReset>
@@ -222,6 +240,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
     __shared__ long long wsum_sh[kThreadsM / 32];
     __shared__ int cut_sh[2];
     __shared__ int cost_sh[2 * 256];
+    __shared__ unsigned seg_sh[2 * 256];
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = a.stages, T = a.T;
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
     }
     if (warp == kIssuerWarpM) tmem_alloc(&tmem_base_sh, 512);
     __syncthreads();
-    split_multi(a, cost_sh, wsum_sh, cut_sh, cls_sm);
+    split_multi(a, cost_sh, wsum_sh, cut_sh, cls_sm, seg_sh);
     const int i0 = cut_sh[0], i1 = cut_sh[1], n_items = i1 - i0;
     const bool cls_cached = n_items <= kClsCapM;
     tc_fence_before();
