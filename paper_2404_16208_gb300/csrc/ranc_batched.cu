@@ -102,10 +102,11 @@ struct TickArgs {
     long long spitch;
     uint32_t sclock;           // stamp clock of this tick (== tick mod 16); its cycle is (sclock >> 4) mod 256
     int all_active;            // every row may hold bits (imported state): no item is idle
-    const uint8_t *core_flags; // [C] bit 0: some input line drives the core; bit 1: its idle ticks can be deferred
+    const uint8_t *core_flags; // [C] bit 0: some input line drives the core; bit 1: its idle ticks can be deferred;
+                               // bit 2: some neuron of the core sends its spikes to the output bus
     const uint8_t *pend_in;    // [items] idle ticks deferred before this tick
     uint8_t *pend_out;         // [items] idle ticks deferred after this tick
-    int cost_active, cost_idle, cost_lazy, cost_wake, cost_first;  // relative costs for the split of the items over the CTAs
+    int cost_active, cost_idle, cost_lazy, cost_wake, cost_out;  // relative costs for the split of the items over the CTAs
     unsigned long long *item_ticks;  // [3]: items updated, items whose tick was deferred, active items (accumulated)
     int stall_test;            // failure-detection tests only: CTA 0 waits for a weight copy on a barrier
                                // armed with a transaction count that no copy satisfies
@@ -155,11 +156,12 @@ __device__ __forceinline__ int item_class(const TickArgs &a, int it) {
 // holds the class of each of its items (bit 2: deferred idle ticks before
 // this tick); pend_out holds the deferred ticks after this tick of each of its
 // items; flags_sh bit 0 is set when some item applies deferred ticks in this
-// tick, bit 1 when some item starts deferring (its spike masks are cleared);
-// bit k of nl_bits[0] is set when item i0 + k is not lazy, of nl_bits[1]
-// when it starts deferring, of nl_bits[2] when it applies deferred ticks.  A
-// range that does not fit kClsCap defers nothing: its lazy items are updated
-// as idle ones (and only flags_sh and pend_out are written).
+// tick; bit k of nl_bits[0] is set when item i0 + k is not lazy, of
+// nl_bits[1] when it applies deferred ticks.  A range that does not fit
+// kClsCap defers nothing: its lazy items are updated as idle ones (and only
+// flags_sh and pend_out are written).  A lazy item's spike masks are left as
+// they are: its last tick fired nothing, and the pass that applies deferred
+// ticks before a state read clears them.
 __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, int *cut_sh, uint8_t *cls_sm,
                                          int *flags_sh, uint32_t (*nl_bits)[kClsCap / 32]) {
     // The arguments this function reads, once (a reference to the kernel's
@@ -170,7 +172,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const int items = a.items, T = a.T;
     const bool all_active = a.all_active != 0, first = a.v0 != nullptr, inputs = a.tick < (long long)a.in_ticks;
     const uint8_t cycle = (uint8_t)(a.sclock >> 4);
-    const int c_act = a.cost_active, c_idle = a.cost_idle, c_lazy = a.cost_lazy, c_wake = a.cost_wake, c_first = a.cost_first;
+    const int c_act = a.cost_active, c_idle = a.cost_idle, c_lazy = a.cost_lazy, c_wake = a.cost_wake, c_out = a.cost_out;
     // As class_from, on those copies.
     auto cls_from = [&](uint8_t stamp, uint8_t pend, uint8_t cflags) -> int {
         if (all_active || stamp == cycle || (inputs && (cflags & 1))) return 2;
@@ -183,8 +185,8 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const int per = ((items + kThreads - 1) / kThreads + 15) & ~15;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t0 = min(items, tid * per), t1 = min(items, t0 + per);
-    for (int w = tid; w < 3 * kClsCap / 32; w += kThreads) nl_bits[w / (kClsCap / 32)][w % (kClsCap / 32)] = 0u;
-    // fn(it, class, deferred idle ticks) for the items [u0, u1) of this thread.
+    for (int w = tid; w < 2 * kClsCap / 32; w += kThreads) nl_bits[w / (kClsCap / 32)][w % (kClsCap / 32)] = 0u;
+    // fn(it, class, deferred idle ticks, core flags) for the items [u0, u1) of this thread.
     auto visit = [&](int u0, int u1, auto &&fn) {
         if (u0 >= u1) return;
         int c = u0 / T, j = u0 - c * T;
@@ -208,14 +210,15 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
                 }
                 ++j;
                 const uint8_t pn = (uint8_t)(pw[k >> 2] >> (8 * (k & 3)));
-                fn(it, cls_from((uint8_t)(sw[k >> 2] >> (8 * (k & 3))), pn, cf), first ? 0 : (int)pn);
+                fn(it, cls_from((uint8_t)(sw[k >> 2] >> (8 * (k & 3))), pn, cf), first ? 0 : (int)pn, cf);
             }
         }
     };
     // Cost of an item: its class, plus the pass that applies deferred ticks
-    // when it wakes up, plus the spike-mask clearing of a first lazy tick.
-    auto cost_of = [&](int cls, int pend) -> int {
-        return (cls == 2 ? c_act : cls == 1 ? c_idle : c_lazy) + (cls != 0 && pend ? c_wake : 0) + (cls == 0 && !pend ? c_first : 0);
+    // when it wakes up, plus the output-bus events of an updated item of an
+    // output core.
+    auto cost_of = [&](int cls, int pend, uint8_t cf) -> int {
+        return (cls == 2 ? c_act : cls == 1 ? c_idle : c_lazy) + (cls != 0 && pend ? c_wake : 0) + (cls != 0 && (cf & 4) ? c_out : 0);
     };
     // Total cost of this thread's items.  A group of 16 items inside one core
     // is classified four at a time (bytes of the stamp and deferral vectors,
@@ -226,7 +229,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
         for (int b16 = t0; b16 < t1; b16 += 16) {
             const int c = b16 / T;
             if (b16 + 16 > t1 || (b16 + 15) / T != c) {
-                visit(b16, min(b16 + 16, t1), [&](int, int cls, int pend) { csum += cost_of(cls, pend); });
+                visit(b16, min(b16 + 16, t1), [&](int, int cls, int pend, uint8_t cf) { csum += cost_of(cls, pend, cf); });
                 continue;
             }
             const uint4 sv = *reinterpret_cast<const uint4 *>(stamp_row + b16);
@@ -234,7 +237,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
             const uint8_t cf = core_flags[c];
             const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w}, pw[4] = {pv.x, pv.y, pv.z, pv.w};
             const bool act_all = all_active || (inputs && (cf & 1)), lazy_ok = !first && (cf & 2);
-            int n_act = 0, n_idle = 0, n_lazy = 0, n_wake = 0, n_lz0 = 0;
+            int n_act = 0, n_idle = 0, n_lazy = 0, n_wake = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {  // byte masks: 0xFF where the item is in the class
                 const uint32_t ma = act_all ? 0xFFFFFFFFu : __vcmpeq4(sw[q], cyc4);
@@ -245,10 +248,9 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
                 n_lazy += __popc(ml) >> 3;
                 n_idle += __popc(mi) >> 3;
                 n_wake += __popc(~ml & mp) >> 3;
-                n_lz0 += __popc(ml & ~mp) >> 3;
             }
             csum += (long long)c_act * n_act + (long long)c_idle * n_idle + (long long)c_lazy * n_lazy +
-                    (long long)c_wake * n_wake + (long long)c_first * n_lz0;
+                    (long long)c_wake * n_wake + ((cf & 4) ? (long long)c_out * (n_act + n_idle) : 0);
         }
     }
     long long cinc = csum;
@@ -279,10 +281,10 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
         if (!walk0) n0 = Pend <= lo ? t1 - t0 : 0;
         if (!walk1) n1 = Pend <= hi ? t1 - t0 : 0;
         if (walk0 || walk1)
-            visit(t0, t1, [&](int, int cls, int pend) {
+            visit(t0, t1, [&](int, int cls, int pend, uint8_t cf) {
                 if (walk0) n0 += P < lo;
                 if (walk1) n1 += P < hi;
-                P += cost_of(cls, pend);
+                P += cost_of(cls, pend, cf);
             });
         n0 = __reduce_add_sync(0xffffffffu, n0);
         n1 = __reduce_add_sync(0xffffffffu, n1);
@@ -295,7 +297,7 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
     const int i0 = cut_sh[0], i1 = cut_sh[1];
     const bool cls_cached = i1 - i0 <= kClsCap;
     int fl = 0, n_up = 0, n_def = 0, n_act = 0;
-    visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend) {
+    visit(max(t0, i0), min(t1, i1), [&](int it, int cls, int pend, uint8_t) {
         if (!cls_cached && cls == 0) cls = 1;
         ++(cls != 0 ? n_up : n_def);
         n_act += cls == 2;
@@ -303,10 +305,9 @@ __device__ __noinline__ void split_items(const TickArgs &a, long long *wsum_sh, 
             const int k = it - i0;
             cls_sm[k] = (uint8_t)(cls | (pend ? 4 : 0));
             if (cls != 0) atomicOr(&nl_bits[0][k >> 5], 1u << (k & 31));
-            if (cls == 0 && !pend) atomicOr(&nl_bits[1][k >> 5], 1u << (k & 31));
-            if (cls != 0 && pend) atomicOr(&nl_bits[2][k >> 5], 1u << (k & 31));
+            if (cls != 0 && pend) atomicOr(&nl_bits[1][k >> 5], 1u << (k & 31));
         }
-        fl |= (pend && cls != 0 ? 1 : 0) | (!pend && cls == 0 ? 2 : 0);
+        fl |= pend && cls != 0 ? 1 : 0;
         pend_out[it] = cls == 0 ? (uint8_t)(pend + 1) : (uint8_t)0;
     });
     if (fl) atomicOr(flags_sh, fl);
@@ -326,8 +327,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
     __shared__ volatile int abort_sh;
     __shared__ long long wsum_sh[kThreads / 32];
     __shared__ int cut_sh[2];
-    __shared__ uint32_t nl_sh[3][kClsCap / 32];  // bit k: item i0 + k is not lazy / starts deferring / wakes up
-    __shared__ int flags_sh;  // bit 0: some item applies deferred idle ticks; bit 1: some item starts deferring
+    __shared__ uint32_t nl_sh[2][kClsCap / 32];  // bit k: item i0 + k is not lazy / wakes up
+    __shared__ int flags_sh;  // bit 0: some item applies deferred idle ticks
 
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int NH = a.NH, KB = a.KB, C = a.C, A = a.A, N = a.N, T = a.T;
@@ -492,16 +493,9 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
             }
         };
         if (flags_sh & 1) {
-            if (cls_cached) for_bits(nl_sh[2], wake);
+            if (cls_cached) for_bits(nl_sh[1], wake);
             else for (int li = 0; li < n_items; ++li) wake(li);
         }
-        // Items that start deferring in this tick: their spike masks are zero
-        // (and stay so while they keep deferring).
-        if (flags_sh & 2)
-            for_bits(nl_sh[1], [&](int li) {
-                const int it = i0 + li, c = it / T, j = it % T;
-                for (int k = 0; k < nu; ++k) a.spk[(((size_t)j * C + c) * 4 + cc0 + k) * N + n] = 0u;
-            });
         // Lazy items take neither a build nor an epilogue (their tick is
         // recorded by the split); an idle item's operand is zero (its row and
         // inputs are known to be empty).  The row words of the next active
@@ -848,10 +842,18 @@ __global__ void batched_reset_v(VT *V, const int *v0, int C, int N, long long ve
 
 // Applies the idle ticks that lazy items deferred: V <- max(V + k * leak,
 // theta-) for k = pend[c * T + j] (exact: the result lies in [theta-, V];
-// formed in 64 bits, since k * leak may not fit 32).
-// Vector e of the interleaved layout as in batched_reset_v.
+// formed in 64 bits, since k * leak may not fit 32), and clears their spike
+// masks (a lazy tick fires nothing; the tick kernel leaves them as they were).
+// Vector e of the interleaved layout as in batched_reset_v; spike word w of
+// spk [T][C][4][N].
 template <typename VT>
-__global__ void batched_catch_up(VT *V, const uint8_t *pend, const int4 *prm, int C, int N, int T, long long vecs) {
+__global__ void batched_catch_up(VT *V, uint32_t *spk, const uint8_t *pend, const int4 *prm, int C, int N, int T, long long vecs) {
+    const long long words = (long long)T * C * 4 * N;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < words; w += (long long)gridDim.x * blockDim.x) {
+        const long long jc = w / (4 * N);
+        const int c = (int)(jc % C), j = (int)(jc / C);
+        if (pend[(size_t)c * T + j]) spk[w] = 0u;
+    }
     constexpr int P = 32 * (int)sizeof(VT) / 16, E = 16 / (int)sizeof(VT);
     uint4 *p = reinterpret_cast<uint4 *>(V);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vecs; e += (long long)gridDim.x * blockDim.x) {
@@ -975,9 +977,13 @@ struct Batched {
     long long spitch = 0;
     bool any_lazy = false;
     // Relative cost of an active, idle and lazy item, of applying deferred
-    // ticks and of a lazy item's first tick (which clears its spike masks);
-    // the split of a tick's items over the CTAs balances their sum.
-    int cost_active = 64, cost_idle = 56, cost_lazy = 1, cost_wake = 40, cost_first = 5;
+    // ticks and of the output-bus events of an updated item of an output
+    // core; the split of a tick's items over the CTAs balances their sum.
+    // Per-CTA busy times of the 512-core MNIST-shaped window against the
+    // CTAs' item mix give about 4.3 us per active item, 3.5 us per idle one,
+    // 18 ns per lazy one, 2.9 us to apply deferred ticks, and 0-1 us more per
+    // item of an output core (growing with its output-bus events).
+    int cost_active = 256, cost_idle = 208, cost_lazy = 1, cost_wake = 168, cost_out = 32;
     CUtensorMap wmap;  // 64-byte aligned by its declaration
 };
 
@@ -1082,7 +1088,8 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
         }
         if (fline.empty()) fline.push_back(0);
     }
-    // Per core: driven by an input line; idle ticks deferrable (item_class).
+    // Per core: driven by an input line; idle ticks deferrable (item_class);
+    // drives the output bus (split cost).
     std::vector<uint8_t> cfl(C, 0);
     for (int c = 0; c < C; c++) {
         const bool driven = fptr[(size_t)c * (A + 1) + A] > fptr[(size_t)c * (A + 1)];
@@ -1092,7 +1099,9 @@ cudaError_t batched_setup(ranc_sim *sim, const ranc_desc *d, std::string &why) {
             const long long pt = d->pos_thr[i];
             ok = d->leak[i] <= 0 && d->neg_thr[i] < pt && d->reset[i] < pt && d->v0[i] < pt;
         }
-        cfl[c] = (uint8_t)((driven ? 1 : 0) | (ok ? 2 : 0));
+        bool out = false;
+        for (int n = 0; n < N && !out; n++) out = d->dest[(size_t)c * N + n].kind == RANC_DEST_OUTPUT;
+        cfl[c] = (uint8_t)((driven ? 1 : 0) | (ok ? 2 : 0) | (out ? 4 : 0));
         bs->any_lazy = bs->any_lazy || ok;
     }
     bs->spitch = ((long long)sim->T * C + 127) / 128 * 128;
@@ -1181,7 +1190,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.pend_in = bs->pend + (size_t)(sim->tick & 1) * bs->spitch;
     a.pend_out = bs->pend + (size_t)((sim->tick + 1) & 1) * bs->spitch;
     a.cost_active = bs->cost_active; a.cost_idle = bs->cost_idle; a.cost_lazy = bs->cost_lazy; a.cost_wake = bs->cost_wake;
-    a.cost_first = bs->cost_first;
+    a.cost_out = bs->cost_out;
     a.item_ticks = bs->item_ticks;
     a.stall_test = sim->stall_test;
     const int grid = std::min(bs->n_sm, a.items);
@@ -1206,11 +1215,11 @@ static cudaError_t batched_materialize(ranc_sim *sim) {
         const long long vecs = (long long)sim->T * sim->C * 4 * sim->N * (sim->vmode == kVInt32 ? 8 : 4);
         const unsigned g = (unsigned)grid_for(vecs);
         if (sim->vmode == kVHalf)
-            batched_catch_up<__half><<<g, 256, 0, sim->stream>>>((__half *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+            batched_catch_up<__half><<<g, 256, 0, sim->stream>>>((__half *)sim->V, sim->spk, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
         else if (sim->vmode == kVInt16)
-            batched_catch_up<int16_t><<<g, 256, 0, sim->stream>>>((int16_t *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+            batched_catch_up<int16_t><<<g, 256, 0, sim->stream>>>((int16_t *)sim->V, sim->spk, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
         else
-            batched_catch_up<int><<<g, 256, 0, sim->stream>>>((int *)sim->V, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
+            batched_catch_up<int><<<g, 256, 0, sim->stream>>>((int *)sim->V, sim->spk, pend_cur, sim->prm, sim->C, sim->N, sim->T, vecs);
         sim->launches++;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
