@@ -451,6 +451,9 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     __shared__ uint32_t red[kMaxStepUnits][4];
     __shared__ int act_sh[kMaxStepUnits];
     __shared__ int ub_sh[kMaxStepUnits], uc_sh[kMaxStepUnits];  // sample and core of each unit
+    __shared__ long long uv_sh[kMaxStepUnits];  // (b * C + c) * N: the unit's first potential
+    __shared__ long long us_sh[kMaxStepUnits];  // (b * C + c) * NW: the unit's first spike word
+    __shared__ int up_sh[kMaxStepUnits];        // c * N: the unit's first parameter
     __shared__ int s_ok;
     const int N = a.N, AW = a.AW, SW = a.SW, C = a.C;
     const int tid = threadIdx.x, lane = tid & 31, nt = blockDim.x;
@@ -467,17 +470,21 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     for (int i = tid; i < m; i += nt) {
         ub_sh[i] = unit(i) / C;
         uc_sh[i] = unit(i) % C;
+        uv_sh[i] = (long long)unit(i) * N;
+        us_sh[i] = (long long)unit(i) * a.NW;
+        up_sh[i] = unit(i) % C * N;
     }
     // Phase C: thread tid updates neuron tid % N of units (round * upr + tid / N).
     const int upr = nt / N, my_slot = tid / N, my_n = tid % N;
+    // Per-tick counters and activity flags start at zero (each tick zeroes
+    // them again after use, before the grid barrier that ends it).
+    for (int i = tid; i < m * 4; i += nt) red[i / 4][i % 4] = 0u;
+    for (int i = tid; i < m; i += nt) act_sh[i] = 0;
     __syncthreads();
     for (int t = 0; t < n_ticks; ++t) {
         const long long tick = a.tick + t;
         const int r0 = (int)(tick & (kRows - 1));
         // ---- A: rows, inputs, activity
-        for (int i = tid; i < m * 4; i += nt) red[i / 4][i % 4] = 0u;
-        for (int i = tid; i < m; i += nt) act_sh[i] = 0;
-        __syncthreads();
         for (int i = tid; i < m * AW; i += nt) {
             const int k = i / AW;
             uint32_t *row = a.ring + (((size_t)ub_sh[k] * C + uc_sh[k]) * kRows + r0) * AW + (i - k * AW);
@@ -533,27 +540,28 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * upr + my_slot;
                 if (my_slot >= upr || i >= m) break;  // uniform per warp (N is a multiple of 32)
-                vv[q] = a.V[((size_t)ub_sh[i] * C + uc_sh[i]) * N + my_n];
-                pr[q] = a.prm[(size_t)uc_sh[i] * N + my_n];
+                vv[q] = a.V[uv_sh[i] + my_n];
+                pr[q] = a.prm[up_sh[i] + my_n];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * upr + my_slot;
                 if (my_slot >= upr || i >= m) break;
-                const int b = ub_sh[i], c = uc_sh[i], n = my_n;
-                const size_t u = (size_t)b * C + c;
+                const int n = my_n;
+                const long long vo = uv_sh[i];
                 int v = vv[q] + (act_sh[i] ? dvs[i * N + n] : 0) + pr[q].x;
                 const bool fire = v >= pr[q].y;
                 if (fire)
                     v = pr[q].w;
                 else if (v < pr[q].z)
                     v = a.neg_mode ? pr[q].w : pr[q].z;
-                a.V[u * N + n] = v;
+                a.V[vo + n] = v;
                 const unsigned fm = __ballot_sync(0xffffffffu, fire);
-                if (lane == 0) a.spk[u * a.NW + n / 32] = fm;
+                if (lane == 0) a.spk[us_sh[i] + n / 32] = fm;
                 uint32_t kind = 0u;
                 if (fire) {
-                    const uint2 d = a.dst[(size_t)c * N + n];
+                    const int b = ub_sh[i];
+                    const uint2 d = a.dst[(size_t)up_sh[i] + n];
                     kind = dest_kind(d);
                     if (kind == RANC_DEST_CORE) {
                         const uint32_t ax = dest_axon(d);
@@ -575,11 +583,13 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
             }
         }
         __syncthreads();
-        for (int i = tid; i < m * 4; i += nt) {
+        for (int i = tid; i < m * 4; i += nt) {  // each thread zeroes what it read
             const int k = i >> 2;
             if (ub_sh[k] < a.n_valid && red[k][i & 3])
                 a.cnt[((size_t)ub_sh[k] * C + uc_sh[k]) * 4 + (i & 3)] += red[k][i & 3];
+            red[k][i & 3] = 0u;
         }
+        for (int i = tid; i < m; i += nt) act_sh[i] = 0;  // read by phase C, before the barrier above
         // Failure-detection test: CTA 0 does not arrive at the first barrier.
         if (!grid_sync(bar, gridDim.x, gen, &s_ok, a.stall_test && blockIdx.x == 0 && t == 0)) {
             if (tid == 0) atomicExch(a.err, kErrTimeout);
