@@ -446,7 +446,7 @@ cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
 
 constexpr int kMaxStepUnits = 64;  // units per CTA and tick held in shared memory
 
-__global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a, int n_ticks, unsigned *bar) {
+__global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a, int n_ticks, unsigned *bar, int resident) {
     extern __shared__ __align__(16) uint32_t smp[];
     __shared__ uint32_t red[kMaxStepUnits][4];
     __shared__ int act_sh[kMaxStepUnits];
@@ -464,6 +464,11 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     uint32_t *spb = sb + m * AW;                                    // [SW] sorted active axons of one unit
     uint16_t *perm = reinterpret_cast<uint16_t *>(spb + SW);        // [SW * 32]
     int8_t *wt = reinterpret_cast<int8_t *>(perm + SW * 32);        // [SW]
+    // With `resident`, the potentials and parameters of the CTA's units stay in
+    // shared memory for the whole launch (the units are the same every tick):
+    // loaded here, written back after the last tick.
+    int4 *prs = reinterpret_cast<int4 *>(smp + (((size_t)m * N + (size_t)m * AW + SW + (SW * 32 + 1) / 2 + (SW + 3) / 4 + 3) & ~(size_t)3));
+    int *vs = reinterpret_cast<int *>(prs + (size_t)m * N);         // [m][N]
     auto unit = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };  // b * C + c
     unsigned gen = 0;
     if (tid == 0) s_ok = 1;
@@ -476,6 +481,13 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
     }
     // Phase C: thread tid updates neuron tid % N of units (round * upr + tid / N).
     const int upr = nt / N, my_slot = tid / N, my_n = tid % N;
+    __syncthreads();
+    if (resident)
+        for (int i = tid; i < m * N; i += nt) {
+            const int k = i / N, n = i - k * N;
+            vs[i] = a.V[uv_sh[k] + n];
+            prs[i] = a.prm[up_sh[k] + n];
+        }
     // Per-tick counters and activity flags start at zero (each tick zeroes
     // them again after use, before the grid barrier that ends it).
     for (int i = tid; i < m * 4; i += nt) red[i / 4][i % 4] = 0u;
@@ -540,8 +552,8 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * upr + my_slot;
                 if (my_slot >= upr || i >= m) break;  // uniform per warp (N is a multiple of 32)
-                vv[q] = a.V[uv_sh[i] + my_n];
-                pr[q] = a.prm[up_sh[i] + my_n];
+                vv[q] = resident ? vs[i * N + my_n] : a.V[uv_sh[i] + my_n];
+                pr[q] = resident ? prs[i * N + my_n] : a.prm[up_sh[i] + my_n];
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -555,7 +567,8 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
                     v = pr[q].w;
                 else if (v < pr[q].z)
                     v = a.neg_mode ? pr[q].w : pr[q].z;
-                a.V[vo + n] = v;
+                if (resident) vs[i * N + n] = v;
+                else a.V[vo + n] = v;
                 const unsigned fm = __ballot_sync(0xffffffffu, fire);
                 if (lane == 0) a.spk[us_sh[i] + n / 32] = fm;
                 uint32_t kind = 0u;
@@ -596,10 +609,16 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
             return;
         }
     }
+    if (resident)  // every update is in shared memory: the last grid barrier synchronised the CTA
+        for (int i = tid; i < m * N; i += nt) {
+            const int k = i / N;
+            a.V[uv_sh[k] + (i - k * N)] = vs[i];
+        }
 }
 
-size_t plain_steps_smem(int m, int N, int AW, int SW) {
-    return (size_t)m * N * 4 + (size_t)m * AW * 4 + (size_t)SW * 4 + (size_t)SW * 32 * 2 + (size_t)SW + 16;
+size_t plain_steps_smem(int m, int N, int AW, int SW, bool resident) {
+    const size_t words = ((size_t)m * N + (size_t)m * AW + SW + (SW * 32 + 1) / 2 + (SW + 3) / 4 + 3) & ~(size_t)3;
+    return words * 4 + (resident ? (size_t)m * N * 20 : 16);
 }
 
 // n_ticks ticks of the plain path in one cooperative launch; the grid is the
@@ -615,7 +634,9 @@ cudaError_t launch_plain_steps(const PlainArgs &a, int n_ticks, unsigned *bar, c
     const long long grid = std::min<long long>(units, n_sm);  // one CTA per SM
     const int m = (int)((units + grid - 1) / grid);
     if (m > kMaxStepUnits) return cudaErrorCooperativeLaunchTooLarge;
-    const size_t smem = plain_steps_smem(m, a.N, a.AW, a.SW);
+    // Potentials and parameters resident in shared memory when they fit.
+    int resident = plain_steps_smem(m, a.N, a.AW, a.SW, true) <= 200 * 1024 ? 1 : 0;
+    const size_t smem = plain_steps_smem(m, a.N, a.AW, a.SW, resident != 0);
     if (smem > 200 * 1024) return cudaErrorCooperativeLaunchTooLarge;  // per-tick launches instead
     if ((e = raise_smem_limit((const void *)plain_steps_kernel, (int)smem)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, plain_steps_kernel, threads, smem)) != cudaSuccess)
@@ -623,7 +644,7 @@ cudaError_t launch_plain_steps(const PlainArgs &a, int n_ticks, unsigned *bar, c
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     if ((e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
     PlainArgs args = a;
-    void *params[] = {&args, &n_ticks, &bar};
+    void *params[] = {&args, &n_ticks, &bar, &resident};
     return cudaLaunchCooperativeKernel((const void *)plain_steps_kernel, dim3((unsigned)grid), dim3(threads), params, smem, s);
 }
 

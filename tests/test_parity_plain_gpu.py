@@ -195,16 +195,11 @@ def test_kernel_timing_and_launch_count(ranc):
     sim.close()
 
 
-def test_persistent_steps_with_more_units_than_ctas(ranc, oracle_mod):
-    """ranc_step(n) on the plain path runs n ticks in one persistent launch
-    whose CTAs serve several (sample, core group) units each: a 64 x 64 grid
-    of 32 x 32 cores, 4 samples (512 units), against the oracle and against
-    per-tick launches, with checks in the middle of the run."""
-    net = W.random_net(77, 64, 64, axons=32, neurons=32, n_types=4, delay_max=6, n_inputs=300,
-                       fanout_per_line=8, p_core=0.6, p_out=0.2, w_lim=7, weight_bits=4, pthr=(1, 12),
-                       nthr=(-12, -1), leak=(-2, 1), v0=(-2, 2))
-    B, T = 4, 14
-    x = W.rate_coded_inputs(5, B, 10, net.n_inputs, 0.3)
+def _persistent_steps_case(ranc, oracle_mod, net, B, T, seed):
+    """ranc_step(k) in one persistent launch (checked by the launch count)
+    against the oracle's trace and against per-tick launches, with state
+    reads between the calls."""
+    x = W.rate_coded_inputs(seed, B, 10, net.n_inputs, 0.3)
     ref = oracle_mod.run(net, x, T, trace=True, n_threads=NPROC)
     a = ranc.Sim(net, B, ranc.RANC_PATH_PLAIN)
     b = ranc.Sim(net, B, ranc.RANC_PATH_PLAIN)
@@ -212,13 +207,15 @@ def test_persistent_steps_with_more_units_than_ctas(ranc, oracle_mod):
         s.load_inputs(x)
     t = 0
     for k in (5, 2, 7):
+        l0 = ranc.ranc_launch_count(a.h)
         a.step(k)
+        assert ranc.ranc_launch_count(a.h) - l0 == 1, "one persistent launch"
         for _ in range(k):
             b.step(1)
         t += k
         va, sa, da = a.state()
         np.testing.assert_array_equal(va, ref["v_trace"][:, t - 1], err_msg=f"tick {t - 1}")
-        np.testing.assert_array_equal(unpack_spikes(sa, 32), ref["spike_trace"][:, t - 1])
+        np.testing.assert_array_equal(unpack_spikes(sa, net.neurons), ref["spike_trace"][:, t - 1])
         assert da == b.state()[2]
     np.testing.assert_array_equal(a.outputs(), ref["out"])
     np.testing.assert_array_equal(a.counters()[:4], ref["counters"][:, :4].sum(0))
@@ -226,3 +223,24 @@ def test_persistent_steps_with_more_units_than_ctas(ranc, oracle_mod):
     assert ref["counters"][:, 1].sum() > 0
     a.close()
     b.close()
+
+
+def test_persistent_steps_with_more_units_than_ctas(ranc, oracle_mod):
+    """ranc_step(n) on the plain path runs n ticks in one persistent launch
+    whose CTAs serve several (sample, core) units each: a 64 x 32 grid of
+    32 x 32 cores, 4 samples (8192 units, 54 per CTA; potentials and
+    parameters resident in shared memory)."""
+    net = W.random_net(77, 64, 32, axons=32, neurons=32, n_types=4, delay_max=6, n_inputs=300,
+                       fanout_per_line=8, p_core=0.6, p_out=0.2, w_lim=7, weight_bits=4, pthr=(1, 12),
+                       nthr=(-12, -1), leak=(-2, 1), v0=(-2, 2))
+    _persistent_steps_case(ranc, oracle_mod, net, 4, 14, 5)
+
+
+def test_persistent_steps_potentials_in_global_memory(ranc, oracle_mod):
+    """The same with 1024-neuron cores (1600 cores, batch 1, 11 units per
+    CTA): the units' potentials and parameters do not fit shared memory, so
+    the launch reads and writes them in global memory every tick."""
+    net = W.random_net(78, 40, 40, axons=32, neurons=1024, n_types=4, delay_max=6, n_inputs=300,
+                       fanout_per_line=8, p_core=0.6, p_out=0.2, w_lim=7, weight_bits=4, pthr=(1, 12),
+                       nthr=(-12, -1), leak=(-2, 1), v0=(-2, 2))
+    _persistent_steps_case(ranc, oracle_mod, net, 1, 14, 6)
