@@ -102,6 +102,33 @@ def test_persistent_grid_barrier_wait_gives_up_and_reset_recovers(ranc, oracle_m
     sim.close()
 
 
+def test_persistent_steps_barrier_wait_gives_up_and_reset_recovers(ranc, oracle_mod, monkeypatch):
+    """ranc_step(n >= 2) on the plain path (one cooperative launch): CTA 0
+    skips its arrival at the first grid barrier, every CTA's bounded wait
+    runs out, the call reports RANC_ETIMEOUT, the handle refuses work until
+    ranc_reset, and then steps correctly."""
+    net = W.tiny_5core()
+    x = W.rate_coded_inputs(7, 2, 8, 784, 0.15)
+    monkeypatch.setenv("RANC_TEST_STALL_WAIT", "1")
+    sim = ranc.Sim(net, 2, ranc.RANC_PATH_PLAIN)
+    monkeypatch.delenv("RANC_TEST_STALL_WAIT")
+    sim.load_inputs(x)
+    t0 = time.time()
+    with pytest.raises(ranc.RancError) as ei:
+        sim.step(5)
+        sim.outputs()
+    assert ei.value.code == ranc.RANC_ETIMEOUT
+    assert time.time() - t0 < 20
+    with pytest.raises(ranc.RancError) as ei:
+        sim.step(5)
+    assert ei.value.code == ranc.RANC_ESTATE
+    sim.reset()
+    sim.load_inputs(x)
+    sim.step(9)
+    np.testing.assert_array_equal(sim.outputs(), oracle_mod.run(net, x, 9)["out"])
+    sim.close()
+
+
 def test_batched_weight_copy_wait_gives_up_and_reset_recovers(ranc, oracle_mod, monkeypatch):
     net = W.tiny_5core()
     x = W.rate_coded_inputs(7, 130, 8, 784, 0.15)

@@ -37,7 +37,9 @@ def test_truenorth_ref_plain_500_ticks(ranc, oracle_mod, net):
     sim.step(3)
     ref = oracle_mod.run(net, np.zeros((1, 0, 0), np.uint32), 3, n_threads=NPROC)
     np.testing.assert_array_equal(sim.state(want_spikes=False, want_digest=False)[0], ref["v"])
+    l0 = ranc.ranc_launch_count(sim.h)
     sim.step(497)
+    assert ranc.ranc_launch_count(sim.h) - l0 == 1  # one persistent launch for the 497 ticks
     v, s, _ = sim.state(want_digest=False)
     np.testing.assert_array_equal(v[0], closed_form(net, 500))
     assert not s.any()
