@@ -23,13 +23,21 @@ def ranc():
     return mod
 
 
-def stream_parity(ranc, oracle_mod, net, x, T, path, runs=1):
-    """x [B, n_in, words]: every batch slot is one stream."""
+def stream_parity(ranc, oracle_mod, net, x, T, path, runs=1, launches=None):
+    """x [B, n_in, words]: every batch slot is one stream.  launches:
+    "persistent" (the whole stream in one tick-kernel launch, besides the
+    reset) or "per_tick" (at least one launch per tick)."""
     B = x.shape[0]
     ref = oracle_mod.run(net, x, T, n_threads=NPROC, out_trace=True)
     sim = ranc.Sim(net, B, path)
     for r in range(runs):  # a run resets the state, so every run matches the oracle again
+        l0 = ranc.ranc_launch_count(sim.h)
         log = sim.run_stream(x, T)
+        n = ranc.ranc_launch_count(sim.h) - l0
+        if launches == "persistent":
+            assert n <= 3, n
+        elif launches == "per_tick":
+            assert n >= T, n
         np.testing.assert_array_equal(log, ref["out_trace"], err_msg=f"run {r}")
         np.testing.assert_array_equal(sim.outputs(), ref["out"])
         v, _, _ = sim.state()
@@ -50,14 +58,14 @@ def random_stream_net(seed):
 def test_plain_persistent_single_stream(ranc, oracle_mod):
     net = random_stream_net(41)
     x = W.rate_coded_inputs(41, 1, 40, net.n_inputs, 0.3)
-    ref = stream_parity(ranc, oracle_mod, net, x, 48, ranc.RANC_PATH_PLAIN, runs=2)
+    ref = stream_parity(ranc, oracle_mod, net, x, 48, ranc.RANC_PATH_PLAIN, runs=2, launches="persistent")
     assert ref["out_trace"].sum() > 0
 
 
 def test_plain_persistent_three_streams(ranc, oracle_mod):
     net = random_stream_net(42)
     x = W.rate_coded_inputs(42, 3, 30, net.n_inputs, 0.3)
-    stream_parity(ranc, oracle_mod, net, x, 37, ranc.RANC_PATH_PLAIN)
+    stream_parity(ranc, oracle_mod, net, x, 37, ranc.RANC_PATH_PLAIN, launches="persistent")
 
 
 def test_plain_per_tick_launches_when_the_grid_does_not_fit(ranc, oracle_mod):
@@ -65,7 +73,7 @@ def test_plain_per_tick_launches_when_the_grid_does_not_fit(ranc, oracle_mod):
     the per-tick launches run (with the log slot of each tick)."""
     net = W.tiny_5core()
     x = W.rate_coded_inputs(43, 200, 20, 784, 0.15)
-    ref = stream_parity(ranc, oracle_mod, net, x, 24, ranc.RANC_PATH_PLAIN)
+    ref = stream_parity(ranc, oracle_mod, net, x, 24, ranc.RANC_PATH_PLAIN, launches="per_tick")
     assert ref["out_trace"].sum() > 0
 
 
@@ -95,8 +103,10 @@ def test_mnist512_stream_device_memory(ranc, oracle_mod):
     dx = torch.from_numpy(x.view(np.int32)).cuda()
     dlog = torch.zeros((1, T, net.n_outputs), dtype=torch.int32, device="cuda")
     sim = ranc.Sim(net, 1, ranc.RANC_PATH_PLAIN)
+    l0 = ranc.ranc_launch_count(sim.h)
     ranc.ranc_run_stream(sim.h, dx.data_ptr(), 64, T, dlog.data_ptr(), ranc.RANC_MEM_DEVICE)
     torch.cuda.synchronize()
+    assert ranc.ranc_launch_count(sim.h) - l0 <= 3  # the 72 ticks in one persistent launch
     np.testing.assert_array_equal(dlog.cpu().numpy().view(np.uint32), ref["out_trace"])
     assert ref["out_trace"].sum() > 0
     np.testing.assert_array_equal(sim.outputs(), ref["out"])
