@@ -221,7 +221,11 @@ def plain_bytes_per_core_tick(net):
             + N // 8)           # spike bitmap
 
 
-POTENTIAL_DTYPE = {
+# Arithmetic types of the batched paths per potential storage format: the
+# crossbar product in fp16 operands with fp32 accumulation, the potential
+# update in the storage type (short code for "dtype", description beside it).
+POTENTIAL_DTYPE = {0: "fp16/int32", 1: "fp16/int16", 2: "fp16"}
+POTENTIAL_DTYPE_NOTE = {
     0: "int32 potentials; fp16 0/1 and weight operands, fp32 accumulate (all exact)",
     1: "int16 potentials; fp16 0/1 and weight operands, fp32 accumulate (all exact)",
     2: "fp16 potentials (integers <= 2048, exact); fp16 0/1 and weight operands, fp32 accumulate (all exact)"}
@@ -543,6 +547,7 @@ def bench_sweep(ranc, torch, steps, warmup, n_cfg=64, core_range=(64, 1024), bat
                       f"{window} ticks, one tick launch for all configurations)",
             "value": n_cfg * batch / sec, "unit": "configuration-samples/s", "higher_is_better": True, "n_gpus": 1,
             "steps": steps, "warmup": warmup, "ms_per_step": ms / steps, "dtype": POTENTIAL_DTYPE[fmt],
+            "dtype_note": POTENTIAL_DTYPE_NOTE[fmt],
             "data": "synthetic (seeded random networks, rate-coded 1024-line inputs, p=0.15)",
             "config": {"workload": f"{n_cfg} networks, {cores} cores in all, core sizes {{128,256,512}}^2, "
                                    f"cores U{{{core_range[0]}..{core_range[1]}}}, weight bits {{4,6,9}}, 2 or 4 types, "
@@ -640,7 +645,7 @@ def other_rows(ranc, torch, steps, warmup):
 
     keep("f1_design_sweep", lambda: bench_sweep(ranc, torch, steps, warmup),
          ("metric", "value", "unit", "ms_per_step", "config", "synaptic_events_per_sec", "launches_per_step",
-          "tuning", "roofline", "parity", "cpu_baseline", "dtype"))
+          "tuning", "roofline", "parity", "cpu_baseline", "dtype", "dtype_note"))
     keep("f4_crossbar_formulations", lambda: bench_xbar(ranc, torch, max(steps, 3), warmup),
          ("metric", "unit", "config", "forms", "fastest", "parity"))
     keep("f3_truenorth_ref", lambda: bench_truenorth(ranc, torch, steps, warmup),
@@ -855,6 +860,7 @@ def main():
         "metric": METRIC, "value": samples_total / (ms_b * 1e-3), "unit": "samples/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": POTENTIAL_DTYPE[fmt],
+        "dtype_note": POTENTIAL_DTYPE_NOTE[fmt],
         "data": "synthetic",
         "synaptic_events_per_sec": br["events"] * ws / (ms_b * 1e-3),
         "config": {"workload": f"mnist-shaped 512-core net (256x256 cores), batched path, {nb} samples x "
