@@ -710,8 +710,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(steps_ms) / len(steps_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "synaptic_events_per_sec": tot_ev / sec,
-            "config": {"workload": "mnist-shaped 512-core net, 24-tick windows, CPU oracle",
-                       "samples_per_step": thr},
+            "config": {"workload": f"mnist-shaped 512-core net (256x256 cores), CPU oracle, {thr} samples x "
+                                   f"{WINDOW} ticks per step (a bounded sample of the batched arm's "
+                                   f"{BATCH_SAMPLES}-sample step)",
+                       "path": "oracle", "samples_per_step": thr, "parallelism": f"{thr} host threads"},
             "cpu_baseline": {"value": val, "unit": "samples/s", "cores": thr, "kind": "oracle",
                              "sample": f"{thr} samples of the 512-core workload per step"},
             "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
