@@ -609,11 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                             const uint4 vz = v_splat<VT>(a.v0[(size_t)ce * N + n]);
 #pragma unroll
                             for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vz;
-                        } else {
-                            const uint4 *vp = vaddr(k);
-#pragma unroll
-                            for (int e = 0; e < kVecs; ++e) vb[k % kPre][e] = vp[e * 32];
-                        }
+                        }  // otherwise loaded during the first unit, half by half
                     }
                     uint4 *vout = vaddr(k);
                     uint32_t mask = 0u;
@@ -673,6 +669,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                                 mask |= (fire ? 1u : 0u) << (hf * 16 + i);
                             }
                             store16<VT>(vout, hf, v);
+                        }
+                        if (k == 0 && nu == 2 && !a.v0) {  // this half's vectors are free: the second unit's
+                            const uint4 *vp1 = vaddr(1);
+#pragma unroll
+                            for (int e = 0; e < kVecs / 2; ++e) vb[0][hf * (kVecs / 2) + e] = vp1[(hf * (kVecs / 2) + e) * 32];
                         }
                     }
                     a.spk[(((size_t)je * C + ce) * 4 + cc) * N + n] = mask;
