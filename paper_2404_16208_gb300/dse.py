@@ -89,7 +89,13 @@ class Evaluator:
 
 
 def features(points):
-    return np.stack([p.features() for p in points]).astype(np.float32)
+    """[n, N_FEATURES] float32, row i = points[i].features() (formed column by column)."""
+    col = lambda name: np.array([getattr(p, name) for p in points], dtype=np.float64)
+    rep, neu, wb, nt = col("replicas"), col("neurons"), col("weight_bits"), col("n_types")
+    cols = [rep / D.R_MAX, neu == 256, wb == 4, wb == 6, wb == 9, nt == 4, col("density"),
+            np.log2(col("thr_scale")) / 2 + 0.5, col("leak_max") / 8, col("delay_max") / 15]
+    out = np.stack([np.asarray(c, dtype=np.float64).astype(np.float32) for c in cols], axis=1)
+    return out.reshape(len(points), D.N_FEATURES)
 
 
 class Surrogate:
@@ -123,15 +129,18 @@ class Surrogate:
         return losses
 
     def predict(self, X):
+        """One copy of all rows to the device, forward passes of max_batch
+        rows on consecutive slices, one copy back."""
         import torch
-        out = np.zeros((X.shape[0], 2), np.float32)
-        for a in range(0, X.shape[0], self.max_batch):
-            xb = torch.from_numpy(np.ascontiguousarray(X[a:a + self.max_batch])).cuda()
-            yb = torch.zeros((xb.shape[0], 2), dtype=torch.float32, device="cuda")
-            self.mlp.forward(xb.data_ptr(), xb.shape[0], yb.data_ptr())
-            torch.cuda.synchronize()
-            out[a:a + xb.shape[0]] = yb.cpu().numpy()
-        return out * self.sd + self.mu
+        n, f = X.shape
+        dx = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+        dy = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for a in range(0, n, self.max_batch):
+            b = min(self.max_batch, n - a)
+            self.mlp.forward(dx.data_ptr() + a * f * 4, b, dy.data_ptr() + a * 2 * 4)
+        torch.cuda.synchronize()
+        return dy.cpu().numpy() * self.sd + self.mu
 
 
 def spearman(a, b):
