@@ -569,6 +569,11 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
                 in_axon[p] = d->in_axon[k];
             }
     }
+    {  // most entries of one core group of the persistent window kernel (its input lists go to shared memory)
+        const int G = std::min(kMaxWindowCores, std::max(1, 1024 / N));
+        for (int c0 = 0; c0 < C; c0 += G)
+            sim->in_group_max = std::max(sim->in_group_max, in_ptr[std::min(C, c0 + G)] - in_ptr[c0]);
+    }
     std::vector<int> v0(d->v0, d->v0 + (size_t)C * N);
 
     if (upload(&sim->xbarT, xbarT) != cudaSuccess || upload(&sim->wtype, wtype) != cudaSuccess ||
@@ -860,6 +865,7 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
                                   uint32_t *counts, int mem) {
     WindowArgs w{};
     w.G = std::min(kMaxWindowCores, std::max(1, 1024 / sim->N));
+    w.in_cap = sim->in_group_max;
     w.n_groups = (sim->C + w.G - 1) / w.G;
     w.n_samples = n_samples;
     w.t_in = t_in;
@@ -1147,6 +1153,7 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
 static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in, int n_ticks, uint32_t *dev_log) {
     WindowArgs w{};
     w.G = std::min(kMaxWindowCores, std::max(1, 1024 / sim->N));
+    w.in_cap = sim->in_group_max;
     w.n_groups = (sim->C + w.G - 1) / w.G;
     w.n_samples = sim->B;
     w.t_in = n_in;

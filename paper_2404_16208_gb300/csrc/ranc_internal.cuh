@@ -72,6 +72,7 @@ struct WindowArgs {
     uint32_t *counts;            // [n_samples][n_out] (device) or NULL
     unsigned *bar;               // [2] grid barrier: arrivals, generation
     int stream;                  // inputs read from p.inputs every tick instead of staged in shared memory
+    int in_cap;                  // > 0: the group's (line, axon) entries staged in shared memory (capacity)
     uint32_t *olog;              // NULL, or per-tick output-bus log [n_samples][window][n_out]
 };
 
@@ -115,6 +116,7 @@ struct ranc_sim {
     int8_t *wtype = nullptr;            // plain: [C][SW] type of each word of the type-sorted axon order
     uint16_t *axperm = nullptr;         // plain: [C][SW*32] axon at each type-sorted position
     int SW = 0;                         // plain: words of that order
+    int in_group_max = 0;               // plain: most input-line entries of one window-kernel core group
     int16_t *wnk = nullptr;
     int4 *prm = nullptr;
     uint2 *dst = nullptr;

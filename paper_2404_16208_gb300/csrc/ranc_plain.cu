@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     uint16_t *perm = reinterpret_cast<uint16_t *>(spb + (size_t)G * SW);  // [ncores][SW*32] axon at each sorted position
     int8_t *wt = reinterpret_cast<int8_t *>(perm + (size_t)G * SW * 32);  // [ncores][SW] type of each sorted word
     uint32_t *inb = reinterpret_cast<uint32_t *>(wt + (((size_t)G * SW + 15) & ~(size_t)15));  // [t_in][in_words] inputs
+    // With w.in_cap, the group's input-line entries: line, and (core in the group, axon) as one bit position of sb.
+    uint32_t *lns = inb + (w.stream ? 0 : (size_t)w.t_in * a.in_words);  // [in_cap]
+    uint16_t *lpos = reinterpret_cast<uint16_t *>(lns + w.in_cap);       // [in_cap]
     const unsigned nblocks = gridDim.x;
     unsigned gen = 0;
 
@@ -295,6 +298,13 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     const uint32_t kind = dest_kind(dd);
     const int ipw = w.t_in * a.in_words;
     const int ip0 = a.in_ptr[c_first], ip1 = a.in_ptr[c_first + ncores];
+    if (w.in_cap)  // read once per launch instead of every input tick (the first grid barrier orders it)
+        for (int k = ip0 + tid; k < ip1; k += blockDim.x) {
+            int kc = 0;
+            while (kc + 1 < ncores && k >= a.in_ptr[c_first + kc + 1]) ++kc;
+            lns[k - ip0] = (uint32_t)a.in_line[k];
+            lpos[k - ip0] = (uint16_t)(kc * AW * 32 + a.in_axon[k]);
+        }
     uint32_t n_sp = 0, n_pk = 0, n_ou = 0, n_syn = 0;
     uint32_t oc = 0u;  // this neuron's output-bus events in the current window
     int V = v0;
@@ -327,6 +337,15 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                 // from the caller's array, one frame per tick.
                 const uint32_t *in = w.stream ? a.inputs + ((size_t)smp * w.t_in + t) * a.in_words
                                               : inb + (size_t)t * a.in_words;
+                if (w.in_cap)
+                    for (int e = tid; e < ip1 - ip0; e += blockDim.x) {
+                        const uint32_t L = lns[e];
+                        if ((in[L >> 5] >> (L & 31)) & 1u) {
+                            const uint32_t p = lpos[e];
+                            atomicOr(&sb[p >> 5], 1u << (p & 31));
+                        }
+                    }
+                else
                 for (int k = ip0 + tid; k < ip1; k += blockDim.x) {
                     const int L = a.in_line[k];
                     if ((in[L >> 5] >> (L & 31)) & 1u) {
@@ -411,11 +430,15 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
 // Launches plain_window_kernel when its grid fits on the device at once (the
 // barrier needs every CTA resident); returns cudaErrorCooperativeLaunchTooLarge
 // otherwise, so the caller can use the per-tick launches instead.
-cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
+cudaError_t launch_plain_windows(const WindowArgs &w_in, cudaStream_t s) {
+    WindowArgs w = w_in;
     const int threads = w.G * w.p.N;
-    const size_t smem = ((size_t)w.G * w.p.N * w.p.SW + (size_t)w.G * w.p.AW + (size_t)w.G * w.p.SW) * 4 +
+    const size_t base = ((size_t)w.G * w.p.N * w.p.SW + (size_t)w.G * w.p.AW + (size_t)w.G * w.p.SW) * 4 +
                         (size_t)w.G * w.p.SW * 32 * 2 + (((size_t)w.G * w.p.SW + 15) & ~(size_t)15) +
                         (w.stream ? 0 : (size_t)w.t_in * w.p.in_words) * 4;
+    // The input-line entries go to shared memory when they fit (6 bytes each).
+    if (w.in_cap > 0 && base + (size_t)w.in_cap * 6 + 64 > 200 * 1024) w.in_cap = 0;
+    const size_t smem = base + (w.in_cap > 0 ? (size_t)w.in_cap * 6 + 16 : 0);
     cudaError_t e = raise_smem_limit((const void *)plain_window_kernel, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n_sm = 0, per_sm = 0;
@@ -426,7 +449,7 @@ cudaError_t launch_plain_windows(const WindowArgs &w, cudaStream_t s) {
     const int grid = w.n_groups * w.p.B;
     if ((long long)per_sm * n_sm < grid) return cudaErrorCooperativeLaunchTooLarge;
     if ((e = cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s)) != cudaSuccess) return e;
-    void *args[] = {const_cast<WindowArgs *>(&w)};
+    void *args[] = {&w};
     return cudaLaunchCooperativeKernel((const void *)plain_window_kernel, dim3(grid), dim3(threads), args, smem, s);
 }
 
