@@ -63,6 +63,25 @@ __device__ __forceinline__ int integrate_sorted(const uint32_t *sp, const uint32
     return dv;
 }
 
+// The same with the sorted words grouped by type: tb[k] .. tb[k+1] are the
+// words of type k, so a word costs an and, a popc and an add, and each type
+// one multiply by its weight.
+__device__ __forceinline__ int integrate_typed(const uint32_t *sp, const uint32_t *xr, int N, const uint8_t *tb, int K,
+                                               const uint32_t (&wr)[4], uint32_t &syn) {
+    int dv = 0;
+    for (int k = 0; k < K; ++k) {
+        int cnt = 0;
+        for (int w = tb[k]; w < tb[k + 1]; ++w) {
+            const uint32_t sw = sp[w];
+            if (sw == 0u) continue;  // uniform across the core's threads
+            cnt += __popc(sw & xr[(size_t)w * N]);
+        }
+        syn += (uint32_t)cnt;
+        dv += weight_of(wr, k) * cnt;
+    }
+    return dv;
+}
+
 __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
     extern __shared__ __align__(128) uint32_t xs[];  // [SW][N] crossbar of this core (sorted axons), word-major
     __shared__ uint32_t s[kMaxWords];                 // active axons of this tick (original order)
@@ -242,6 +261,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t red[kMaxWindowCores][4];
     __shared__ int s_ok;
+    __shared__ uint8_t tbs[kMaxWindowCores][kMaxTypes + 1];  // sorted words of each type: tbs[kc][k] .. tbs[kc][k+1]
     const PlainArgs &a = w.p;
     const int G = w.G, N = a.N, AW = a.AW, SW = a.SW, C = a.C;
     const int grp = blockIdx.x % w.n_groups, b = blockIdx.x / w.n_groups;
@@ -294,6 +314,15 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
         if (tid == 0) atomicExch(a.err, kErrTimeout);
         mbar_wait_bounded(&bar, 0);
         return;
+    }
+    for (int i = tid; i < ncores * (a.K + 1); i += blockDim.x) {  // ordered before use by the first grid barrier
+        const int kc = i / (a.K + 1), k = i % (a.K + 1);
+        int nw = 0;
+        for (int q = 0; q < SW; ++q) {
+            const int ty = wt[kc * SW + q];
+            nw += (ty >= 0 && ty < k) ? 1 : 0;
+        }
+        tbs[kc][k] = (uint8_t)nw;
     }
     const uint32_t kind = dest_kind(dd);
     const int ipw = w.t_in * a.in_words;
@@ -362,7 +391,7 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
             bool fire = false;
             if (has_core) {
                 uint32_t syn = 0u;
-                const int dv = integrate_sorted(spb + cg * SW, xs + (size_t)cg * SW * N + n, N, wt + cg * SW, SW, wr, syn);
+                const int dv = integrate_typed(spb + cg * SW, xs + (size_t)cg * SW * N + n, N, tbs[cg], a.K, wr, syn);
                 int x = V + dv + lam;
                 fire = x >= pth;
                 if (fire)
