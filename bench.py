@@ -273,7 +273,7 @@ def measure_l2_copy(torch, mib=48, reps=40):
 # ticks (profiles/plain_window_kernel_mnist512_b1.md): crossbars stay in shared
 # memory and parameters in registers, so a tick moves far fewer bytes than the
 # per-tick kernel's algorithmic bytes.
-PLAIN_L2_BYTES_PER_TICK = 521356224 / 480
+PLAIN_L2_BYTES_PER_TICK = 294096608 / 480
 
 
 def oracle_outputs(net, x, n):
