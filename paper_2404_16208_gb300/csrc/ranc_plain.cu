@@ -324,6 +324,21 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
         }
         tbs[kc][k] = (uint8_t)nw;
     }
+    // Gather into the sorted order: the (word, bit) of sb read for each of
+    // this thread's sorted positions is the same every tick; up to two
+    // positions per thread are kept in registers (0xFFFFFFFF: no axon).
+    const int gP = ncores * SW * 32;
+    const bool g_regs = gP <= 2 * (int)blockDim.x;
+    uint32_t gsrc[2] = {0xFFFFFFFFu, 0xFFFFFFFFu};
+    if (g_regs)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = tid + q * (int)blockDim.x;
+            if (i < gP) {
+                const int j = i / (SW * 32), ia = perm[i];
+                if (ia != 0xFFFF) gsrc[q] = ((uint32_t)(j * AW + (ia >> 5)) << 5) | (uint32_t)(ia & 31);
+            }
+        }
     const uint32_t kind = dest_kind(dd);
     const int ipw = w.t_in * a.in_words;
     const int ip0 = a.in_ptr[c_first], ip1 = a.in_ptr[c_first + ncores];
@@ -386,7 +401,19 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                 }
                 __syncthreads();
             }
-            gather_sorted(sb, perm, AW, SW, ncores, spb, tid, blockDim.x);
+            if (g_regs) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int i = tid + q * (int)blockDim.x;
+                    if (i >= ((gP + 31) & ~31)) break;  // uniform per warp
+                    const uint32_t g = gsrc[q];
+                    const bool on = g != 0xFFFFFFFFu && ((sb[g >> 5] >> (g & 31)) & 1u);
+                    const unsigned word = __ballot_sync(0xffffffffu, on);
+                    if ((i & 31) == 0) spb[i >> 5] = word;
+                }
+            } else {
+                gather_sorted(sb, perm, AW, SW, ncores, spb, tid, blockDim.x);
+            }
             __syncthreads();
             bool fire = false;
             if (has_core) {
