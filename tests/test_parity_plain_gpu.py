@@ -94,6 +94,24 @@ def test_run_samples_batch1_like_the_benchmark(ranc, oracle_mod):
     sim.close()
 
 
+def test_run_samples_without_the_shared_memory_shortcuts(ranc, oracle_mod):
+    """The persistent window kernel's two shared-memory shortcuts both off:
+    16 cores of 64 neurons per CTA with 7 sorted words each (3584 sorted
+    positions: more than two per thread, so the gather reads the permutation
+    every tick) and about 28 000 input-line entries per core group (more than
+    shared memory holds, so the entries are read from global memory)."""
+    net = W.random_net(91, 8, 4, axons=128, neurons=64, n_types=4, n_inputs=2000, fanout_per_line=28,
+                       delay_max=5, p_core=0.5, p_out=0.3, n_outputs=6)
+    x = W.rate_coded_inputs(91, 6, 10, net.n_inputs, 0.1)
+    ref = oracle_mod.run(net, x, 14, n_threads=NPROC)
+    sim = ranc.Sim(net, 2, ranc.RANC_PATH_PLAIN)
+    l0 = ranc.ranc_launch_count(sim.h)
+    np.testing.assert_array_equal(sim.run_samples(x, 14), ref["out"])
+    assert ranc.ranc_launch_count(sim.h) - l0 <= 3  # the persistent kernel, not per-tick launches
+    assert ref["out"].sum() > 0
+    sim.close()
+
+
 def test_run_samples_ragged_groups(ranc, oracle_mod):
     net = W.tiny_5core()
     x = W.rate_coded_inputs(3, 11, 8, 784, 0.15)
