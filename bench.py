@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 512 << 20
 # traffic is that times the units it updates.  Valid only for the tick
 # kernel's source it was taken on (kernel_source_sha; see
 # profiles/batched_tick_kernel_mnist512_1024samples.md).
-PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "cf5159628fe13564", "bytes": 394.040320e6 + 237.288192e6,
+PROFILED_TRAFFIC = {"kernel_source_sha256_prefix": "d6c9229f99b304c3", "bytes": 394.113024e6 + 236.777728e6,
                     "units": 1024 * 512}
 
 

@@ -26,6 +26,14 @@
  *   - A handle is not thread-safe: one host thread at a time per handle.
  *   - Samples are independent copies of the network (a batch); sample b of
  *     every array below is the b-th sample.
+ *   - Debug build (libranc_debug.so, compiled with RANC_DEBUG): the tick
+ *     kernels check every index they derive from the description before the
+ *     global access it addresses (input line and axon of an input entry,
+ *     destination core and axon of a packet, output id); a failed check skips
+ *     the access and the next synchronising call returns RANC_ECUDA with
+ *     "range check failed (site k)" in ranc_last_error.  The environment
+ *     variable RANC_DEBUG_PLANT=k, read by ranc_create in that build only,
+ *     fails every check of site k on purpose (test use; cleared by ranc_reset).
  */
 #ifndef RANC_H
 #define RANC_H

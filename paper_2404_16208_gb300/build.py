@@ -2,6 +2,9 @@
 
 The translation units are compiled in parallel with nvcc and linked into one
 shared library against the shared CUDA runtime (the one PyTorch also loads).
+``build(debug=True)`` makes the same library with device-side range checks
+(``-DRANC_DEBUG``) as ``_lib/libranc_debug.so``, for the tests that run the
+kernels under those checks; ``build_all()`` makes both.
 """
 
 import concurrent.futures as cf
@@ -14,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libranc.so")
+LIB_DEBUG = os.path.join(OUT_DIR, "libranc_debug.so")
 UNITS = ("ranc_api.cu", "ranc_plain.cu", "ranc_batched.cu", "ranc_multi.cu", "ranc_xbar.cu", "ranc_mlp.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -35,17 +39,22 @@ def _sources_mtime():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force=False, verbose=False):
-    """Compile (if stale) and return the path of ``libranc.so``."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
+def build(force=False, verbose=False, debug=False):
+    """Compile (if stale) and return the path of ``libranc.so`` (with debug:
+    ``libranc_debug.so``, the kernels' range checks compiled in)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _sources_mtime():
+        return lib
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    if debug:
+        common += ["-DRANC_DEBUG"]
+    tag = ("dbg." if debug else "") + str(os.getpid())
     objs = []
 
     def compile_one(unit):
-        obj = os.path.join(OUT_DIR, unit.replace(".cu", f".{os.getpid()}.o"))
+        obj = os.path.join(OUT_DIR, unit.replace(".cu", f".{tag}.o"))
         cmd = [nvcc] + common + ["-c", os.path.join(SRC, unit), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
@@ -58,7 +67,7 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     libdir = _cuda_lib_dir(nvcc)
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
         "-Xlinker", f"-rpath={libdir}", "-L", libdir]
@@ -66,11 +75,18 @@ def build(force=False, verbose=False):
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError(f"link of libranc.so failed:\n{r.stderr[-4000:]}")
-    os.replace(tmp, LIB)
-    return LIB
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stderr[-4000:]}")
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force=False):
+    """Both libraries, compiled side by side; returns (release, debug) paths."""
+    with cf.ThreadPoolExecutor(2) as ex:
+        rel, dbg = ex.submit(build, force), ex.submit(build, force, False, True)
+        return rel.result(), dbg.result()
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

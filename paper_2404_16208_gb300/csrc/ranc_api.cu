@@ -173,6 +173,7 @@ int check_device_error(ranc_sim *sim) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(sim->stream);
     if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "kernel failure: %s", cudaGetErrorString(e));
     if (h == kErrTimeout) return fail(sim, RANC_ETIMEOUT, "a device-side wait gave up after %llu ns", kWaitLimitNs);
+    if ((h & 0xFF) == kErrBounds) return fail(sim, RANC_ECUDA, "device-side range check failed (site %d)", h >> 8);
     if (h != kErrNone) return fail(sim, RANC_ECUDA, "device error code %d", h);
     return RANC_OK;
 }
@@ -235,6 +236,7 @@ PlainArgs plain_args(const ranc_sim *sim) {
     a.inputs = sim->in_override ? sim->in_override : sim->inputs;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
     a.stall_test = sim->stall_test;
+    a.dbg_plant = sim->dbg_plant;
     a.olog = sim->olog_t; a.olog_stride = sim->olog_stride;
     return a;
 }
@@ -495,6 +497,10 @@ extern "C" int ranc_create(const ranc_desc *d, int32_t batch, int32_t path, void
         const char *st = getenv("RANC_TEST_STALL_WAIT");
         sim->stall_test = (st && *st && *st != '0') ? 1 : 0;
     }
+    if (kDebugBuild) {
+        const char *pl = getenv("RANC_DEBUG_PLANT");
+        sim->dbg_plant = pl ? atoi(pl) : 0;
+    }
     auto abort_create = [&](int code, const std::string &msg) {
         g_alloc_budget = -1;
         g_create_error = msg;
@@ -648,6 +654,10 @@ extern "C" int ranc_create_multi(const ranc_desc *const *descs, int32_t n_networ
     {
         const char *st = getenv("RANC_TEST_STALL_WAIT");
         sim->stall_test = (st && *st && *st != '0') ? 1 : 0;
+    }
+    if (kDebugBuild) {
+        const char *pl = getenv("RANC_DEBUG_PLANT");
+        sim->dbg_plant = pl ? atoi(pl) : 0;
     }
     auto abort_create = [&](int code, const std::string &msg) {
         g_alloc_budget = -1;
@@ -842,7 +852,13 @@ extern "C" int ranc_get_tick(const ranc_sim *sim, int64_t *tick) {
 
 extern "C" int ranc_reset(ranc_sim *sim) {
     if (!sim) return RANC_EINVAL;
+    if ((sim->stall_test || sim->dbg_plant) && sim->win_exec) {  // recorded with the test settings
+        cudaStreamSynchronize(sim->stream);
+        cudaGraphExecDestroy(sim->win_exec);
+        sim->win_exec = nullptr;
+    }
     sim->stall_test = 0;  // a stall-test handle runs normally once reset
+    sim->dbg_plant = 0;
     if (sim->sticky) {
         cudaError_t e = cudaStreamSynchronize(sim->stream);
         if (e != cudaSuccess) return fail(sim, RANC_ECUDA, "device unusable: %s", cudaGetErrorString(e));
@@ -902,6 +918,7 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
     a.stall_test = sim->stall_test;
+    a.dbg_plant = sim->dbg_plant;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sim->timing) {
         if (sim->ev_used + 2 > 4096) {
@@ -1171,6 +1188,7 @@ static int run_stream_persistent(ranc_sim *sim, const uint32_t *dev_in, int n_in
     a.in_ptr = sim->in_ptr; a.in_line = sim->in_line; a.in_axon = sim->in_axon; a.inputs = dev_in;
     a.V = (int *)sim->V; a.ring = sim->ring; a.spk = sim->spk; a.out = sim->out; a.cnt = sim->cnt; a.err = sim->err;
     a.stall_test = sim->stall_test;
+    a.dbg_plant = sim->dbg_plant;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (sim->timing) {
         if (sim->ev_used + 2 > 4096) {

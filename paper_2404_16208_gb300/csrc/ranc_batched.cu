@@ -110,6 +110,7 @@ struct TickArgs {
     unsigned long long *item_ticks;  // [3]: items updated, items whose tick was deferred, active items (accumulated)
     int stall_test;            // failure-detection tests only: CTA 0 waits for a weight copy on a barrier
                                // armed with a transaction count that no copy satisfies
+    int dbg_plant;             // debug builds: site whose range checks fail on purpose (0: none)
 };
 
 constexpr int kPendMax = 250;  // deferred idle ticks of an item are applied before this many accumulate
@@ -456,9 +457,11 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 }
                 if (f1 > f0) {
                     const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
-                    xnext = in[(size_t)ln0 * 2];
+                    if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, ln0, a.Lpad)) xnext = in[(size_t)ln0 * 2];
                     for (int e = f0 + 1; e < f1; ++e) {  // further lines (each waits for its load)
-                        const uint2 y = in[(size_t)a.fin_line[e] * 2];
+                        const int ln = a.fin_line[e];
+                        if (!RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, ln, a.Lpad)) continue;
+                        const uint2 y = in[(size_t)ln * 2];
                         w.x |= y.x;
                         w.y |= y.y;
                     }
@@ -682,7 +685,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                     n_sp += __popc(live);
                     if (mask && kind == RANC_DEST_CORE) {
                         n_pk += __popc(live);
-                        if (nu == 1) {
+                        if (nu == 1 && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, dd.x, C) &&
+                            RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, dest_axon(dd), A)) {
                             const uint32_t ax = dest_axon(dd);
                             const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
                             atomicOr(reinterpret_cast<uint32_t *>(a.ring) + ((((size_t)je * C + dd.x) * kRows + r) * A + ax) * 4 + cc,
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                         const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
                         const uint32_t idL = __shfl_sync(0xffffffffu, dd.x, L);
                         const int bs = je * 128 + cc * 32 + lane;
-                        if ((mL >> lane) & 1u) {
+                        if (((mL >> lane) & 1u) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, idL, a.n_out)) {
                             atomicAdd(a.out + (size_t)bs * a.n_out + idL, 1u);
                             if (a.olog && bs < a.olog_rows) atomicAdd(a.olog + (size_t)bs * a.olog_stride + idL, 1u);
                         }
@@ -713,7 +717,8 @@ __global__ void __launch_bounds__(kThreads, 1) batched_tick_kernel(const __grid_
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 // Two units of one neuron: adjacent words (cc0 even) of the same
                 // destination row, delivered by one 64-bit atomicOr, one stamp.
-                if (nu == 2 && kind == RANC_DEST_CORE && (dm0 | dm1)) {
+                if (nu == 2 && kind == RANC_DEST_CORE && (dm0 | dm1) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, dd.x, C) &&
+                    RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, dest_axon(dd), A)) {
                     const uint32_t ax = dest_axon(dd);
                     const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
                     atomicOr(reinterpret_cast<unsigned long long *>(reinterpret_cast<uint32_t *>(a.ring) +
@@ -1194,6 +1199,7 @@ cudaError_t launch_batched_tick(ranc_sim *sim, const BatchedArgs &) {
     a.cost_out = bs->cost_out;
     a.item_ticks = bs->item_ticks;
     a.stall_test = sim->stall_test;
+    a.dbg_plant = sim->dbg_plant;
     const int grid = std::min(bs->n_sm, a.items);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? batched_tick_kernel<__half, 1> : batched_tick_kernel<__half, 0>)
                 : sim->vmode == kVInt16 ? (sim->neg_mode ? batched_tick_kernel<int16_t, 1> : batched_tick_kernel<int16_t, 0>)

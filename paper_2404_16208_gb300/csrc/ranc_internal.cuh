@@ -21,7 +21,33 @@ constexpr int kVInt32 = 0, kVInt16 = 1, kVHalf = 2;
 constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // static scratch of the allocation-free read
 
 // Device error word values (set by kernels, read by synchronous host calls).
+// kErrBounds carries the site of the failed check in bits 8 and up.
 enum : int { kErrNone = 0, kErrTimeout = 1, kErrBounds = 2 };
+
+// Debug builds (compiled with -DRANC_DEBUG, library libranc_debug.so): every
+// index a kernel derives from the network description before a global access
+// is checked against its range -- the input line of a fan-in entry, the axon
+// of an input entry, the destination core and axon of a spike packet, the
+// output id of an output-bus event.  A failed check skips that access and
+// records kErrBounds | site << 8 in the handle's error word (the first failure
+// is kept); the synchronous call that reads the word returns RANC_ECUDA naming
+// the site.  `plant` (from the RANC_DEBUG_PLANT environment variable at
+// create, debug builds only) fails every check of one site on purpose, so
+// that tests can see a failure reported without any invalid access.  Release
+// builds compile every check to `true`.
+enum : int { kSiteInputLine = 1, kSiteInputAxon = 2, kSiteDestCore = 3, kSiteDestAxon = 4, kSiteOutputId = 5 };
+#ifdef RANC_DEBUG
+constexpr bool kDebugBuild = true;
+__device__ __forceinline__ bool debug_in_range(int *err, int plant, int site, long long i, long long n) {
+    if (i >= 0 && i < n && site != plant) return true;
+    atomicCAS(err, kErrNone, kErrBounds | (site << 8));
+    return false;
+}
+#define RANC_IN_RANGE(err, plant, site, i, n) ::ranc::debug_in_range((err), (plant), (site), (long long)(i), (long long)(n))
+#else
+constexpr bool kDebugBuild = false;
+#define RANC_IN_RANGE(err, plant, site, i, n) true
+#endif
 
 // Resolved destination of a neuron: x = destination core (kind core) or output
 // id (kind output); y = axon | delay << 16 | kind << 24.
@@ -60,6 +86,7 @@ struct PlainArgs {
                                  // kernel); CTA 0 skips its first grid-barrier arrival (persistent kernel)
     uint32_t *olog;              // NULL, or this tick's output-bus log: event (b, id) also adds 1 at
     long long olog_stride;       //   olog[b * olog_stride + id]
+    int dbg_plant;               // debug builds: site whose range checks fail on purpose (0: none)
 };
 
 // Persistent plain path (ranc_run_samples): G cores per CTA, all windows in one launch.
@@ -117,6 +144,7 @@ struct ranc_sim {
     uint16_t *axperm = nullptr;         // plain: [C][SW*32] axon at each type-sorted position
     int SW = 0;                         // plain: words of that order
     int in_group_max = 0;               // plain: most input-line entries of one window-kernel core group
+    int dbg_plant = 0;                  // debug builds: RANC_DEBUG_PLANT at create (see RANC_IN_RANGE)
     int16_t *wnk = nullptr;
     int4 *prm = nullptr;
     uint2 *dst = nullptr;

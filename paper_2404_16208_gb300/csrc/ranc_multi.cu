@@ -124,6 +124,7 @@ struct MultiArgs {
     int kbmax;                 // largest A/64 of the handle: operand blocks kept in shared memory
     int stall_test;            // failure-detection tests only: CTA 0's issuer waits for its first weight
                                // block on a barrier armed with a transaction count no copy satisfies
+    int dbg_plant;             // debug builds: site whose range checks fail on purpose (0: none)
 };
 
 // Split of the items over the CTAs by a cost prefix (as on the single-network
@@ -353,9 +354,11 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                 }
                 if (inputs && f1[t] > f0[t]) {
                     const uint2 *in = reinterpret_cast<const uint2 *>(a.inT + ((size_t)j * a.in_ticks + a.tick) * a.Lpad) + rhf;
-                    wi[t] = in[(size_t)ln0[t] * 2];
+                    if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, ln0[t], a.Lpad)) wi[t] = in[(size_t)ln0[t] * 2];
                     for (int e = f0[t] + 1; e < f1[t]; ++e) {  // further lines (each waits for its load)
-                        const uint2 y = in[(size_t)a.fin_line[e] * 2];
+                        const int ln = a.fin_line[e];
+                        if (!RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, ln, a.Lpad)) continue;
+                        const uint2 y = in[(size_t)ln * 2];
                         wi[t].x |= y.x;
                         wi[t].y |= y.y;
                     }
@@ -529,7 +532,8 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                 const uint32_t live = mask & valid;
                 const uint32_t kind = dest_kind(dd);
                 n_sp += __popc(live);
-                if (mask && kind == RANC_DEST_CORE) {
+                if (mask && kind == RANC_DEST_CORE && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, dd.x, sde.C) &&
+                    RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, dest_axon(dd), sde.A)) {
                     n_pk += __popc(live);
                     const uint32_t ax = dest_axon(dd);
                     const int r = (int)((a.tick + dest_delay(dd)) & (kRows - 1));
@@ -545,7 +549,8 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
                     olanes &= olanes - 1u;
                     const uint32_t mL = __shfl_sync(0xffffffffu, live, L);
                     const uint32_t idL = __shfl_sync(0xffffffffu, dd.x, L);
-                    if ((mL >> lane) & 1u) atomicAdd(a.out + (size_t)(je * 128 + cc * 32 + lane) * a.n_out + idL, 1u);
+                    if (((mL >> lane) & 1u) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, idL, a.n_out))
+                        atomicAdd(a.out + (size_t)(je * 128 + cc * 32 + lane) * a.n_out + idL, 1u);
                 }
             }
             if (stop) break;
@@ -945,7 +950,7 @@ cudaError_t launch_multi_tick(ranc_sim *sim) {
     }
     a.stamp = m->stamp; a.spitch = m->spitch; a.stamp_row = m->stamp + (size_t)(sim->tick & (kRows - 1)) * m->spitch;
     a.sclock = sim->sclock; a.all_active = sim->all_active_ticks > 0; a.core_flags = m->core_flags;
-    a.item_ticks = m->item_ticks; a.kbmax = m->kbmax; a.stall_test = sim->stall_test;
+    a.item_ticks = m->item_ticks; a.kbmax = m->kbmax; a.stall_test = sim->stall_test; a.dbg_plant = sim->dbg_plant;
     const int grid = std::min(m->n_sm, a.items);
     const size_t smem = smem_for(m->kbmax, m->stages);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? multi_tick_kernel<__half, 1> : multi_tick_kernel<__half, 0>)

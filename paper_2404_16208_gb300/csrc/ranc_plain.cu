@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
         const uint32_t *in = a.inputs + ((size_t)b * a.in_ticks + a.tick) * a.in_words;
         for (int k = a.in_ptr[c] + n; k < a.in_ptr[c + 1]; k += blockDim.x) {
             const int L = a.in_line[k];
-            if ((in[L >> 5] >> (L & 31)) & 1u) {
+            if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, L, a.in_words * 32) && ((in[L >> 5] >> (L & 31)) & 1u)) {
                 const int ax = a.in_axon[k];
-                atomicOr(&s[ax >> 5], 1u << (ax & 31));
+                if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputAxon, ax, a.A)) atomicOr(&s[ax >> 5], 1u << (ax & 31));
             }
         }
     }
@@ -184,8 +184,9 @@ __global__ void __launch_bounds__(1024) plain_tick_kernel(const PlainArgs a) {
         if (kind == RANC_DEST_CORE) {
             const uint32_t ax = dest_axon(d);
             const long long r = (a.tick + dest_delay(d)) & (kRows - 1);
-            atomicOr(a.ring + (((size_t)b * a.C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
-        } else if (kind == RANC_DEST_OUTPUT) {
+            if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, d.x, a.C) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, ax, a.A))
+                atomicOr(a.ring + (((size_t)b * a.C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
+        } else if (kind == RANC_DEST_OUTPUT && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, d.x, a.n_out)) {
             atomicAdd(a.out + (size_t)b * a.n_out + d.x, 1u);
             if (a.olog) atomicAdd(a.olog + (size_t)b * a.olog_stride + d.x, 1u);
         }
@@ -384,19 +385,19 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                 if (w.in_cap)
                     for (int e = tid; e < ip1 - ip0; e += blockDim.x) {
                         const uint32_t L = lns[e];
-                        if ((in[L >> 5] >> (L & 31)) & 1u) {
+                        if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, L, a.in_words * 32) && ((in[L >> 5] >> (L & 31)) & 1u)) {
                             const uint32_t p = lpos[e];
-                            atomicOr(&sb[p >> 5], 1u << (p & 31));
+                            if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputAxon, p, ncores * AW * 32)) atomicOr(&sb[p >> 5], 1u << (p & 31));
                         }
                     }
                 else
                 for (int k = ip0 + tid; k < ip1; k += blockDim.x) {
                     const int L = a.in_line[k];
-                    if ((in[L >> 5] >> (L & 31)) & 1u) {
+                    if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, L, a.in_words * 32) && ((in[L >> 5] >> (L & 31)) & 1u)) {
                         int kc = 0;
                         while (kc + 1 < ncores && k >= a.in_ptr[c_first + kc + 1]) ++kc;
                         const int ax = a.in_axon[k];
-                        atomicOr(&sb[kc * AW + (ax >> 5)], 1u << (ax & 31));
+                        if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputAxon, ax, a.A)) atomicOr(&sb[kc * AW + (ax >> 5)], 1u << (ax & 31));
                     }
                 }
                 __syncthreads();
@@ -434,20 +435,21 @@ __global__ void __launch_bounds__(1024, 1) plain_window_kernel(const WindowArgs 
                     if (kind == RANC_DEST_CORE) {
                         const uint32_t ax = dest_axon(dd);
                         const int rr = (t + (int)dest_delay(dd)) & (kRows - 1);
-                        atomicOr(a.ring + (((size_t)b * C + dd.x) * kRows + rr) * AW + (ax >> 5), 1u << (ax & 31));
+                        if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, dd.x, C) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, ax, a.A))
+                            atomicOr(a.ring + (((size_t)b * C + dd.x) * kRows + rr) * AW + (ax >> 5), 1u << (ax & 31));
                         if (valid) ++n_pk;
                     } else if (kind == RANC_DEST_OUTPUT) {
                         ++oc;  // added to the output bus once, at the window's last tick
                         if (valid) {
                             ++n_ou;
-                            if (w.olog)
+                            if (w.olog && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, dd.x, a.n_out))
                                 atomicAdd(w.olog + ((size_t)smp * w.window + t) * a.n_out + dd.x, 1u);
                         }
                     }
                 }
             }
             if (t == w.window - 1 && oc) {
-                atomicAdd(a.out + (size_t)b * a.n_out + dd.x, oc);
+                if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, dd.x, a.n_out)) atomicAdd(a.out + (size_t)b * a.n_out + dd.x, oc);
                 oc = 0u;
             }
             const unsigned fm = __ballot_sync(0xffffffffu, fire);
@@ -594,9 +596,9 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
                 const uint32_t *in = a.inputs + ((size_t)b * a.in_ticks + tick) * a.in_words;
                 for (int k = a.in_ptr[c] + tid; k < a.in_ptr[c + 1]; k += nt) {
                     const int L = a.in_line[k];
-                    if ((in[L >> 5] >> (L & 31)) & 1u) {
+                    if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputLine, L, a.in_words * 32) && ((in[L >> 5] >> (L & 31)) & 1u)) {
                         const int ax = a.in_axon[k];
-                        atomicOr(&sb[i * AW + (ax >> 5)], 1u << (ax & 31));
+                        if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteInputAxon, ax, a.A)) atomicOr(&sb[i * AW + (ax >> 5)], 1u << (ax & 31));
                         act_sh[i] = 1;
                     }
                 }
@@ -658,8 +660,9 @@ __global__ void __launch_bounds__(1024, 1) plain_steps_kernel(const PlainArgs a,
                     if (kind == RANC_DEST_CORE) {
                         const uint32_t ax = dest_axon(d);
                         const long long r = (tick + dest_delay(d)) & (kRows - 1);
-                        atomicOr(a.ring + (((size_t)b * C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
-                    } else if (kind == RANC_DEST_OUTPUT) {
+                        if (RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestCore, d.x, C) && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteDestAxon, ax, a.A))
+                            atomicOr(a.ring + (((size_t)b * C + d.x) * kRows + r) * AW + (ax >> 5), 1u << (ax & 31));
+                    } else if (kind == RANC_DEST_OUTPUT && RANC_IN_RANGE(a.err, a.dbg_plant, kSiteOutputId, d.x, a.n_out)) {
                         atomicAdd(a.out + (size_t)b * a.n_out + d.x, 1u);
                     }
                 }

@@ -106,6 +106,16 @@ def load_library(path=LIB_PATH):
 _lib = load_library()
 
 
+def use_library(path):
+    """Route every later call of this module through the library at `path`
+    (for instance ``_lib/libranc_debug.so``, the build with device-side range
+    checks) and return the one used before.  A handle must be used and
+    destroyed through the library that created it."""
+    global _lib
+    prev, _lib = _lib, load_library(path)
+    return prev
+
+
 def _check(rc, h):
     if rc != RANC_OK:
         raise RancError(rc, _lib.ranc_last_error(h).decode())

@@ -66,6 +66,15 @@ def test_library_exports_every_declared_symbol(ranc):
     assert sorted(ranc.EXPORTED) == declared_functions()
 
 
+def test_debug_library_exports_the_same_symbols(ranc):
+    """The range-checked debug build carries the whole ABI of all three headers."""
+    from paper_2404_16208_gb300 import build as B
+    lib = C.CDLL(B.build(debug=True))
+    for header in ("ranc.h", "ranc_xbar.h", "ranc_mlp.h"):
+        for name in declared_functions(os.path.join(ROOT, "include", header)):
+            assert hasattr(lib, name), (header, name)
+
+
 def test_struct_layout_matches_c(tmp_path, ranc):
     exe = tmp_path / "abi_probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_probe.c"),
