@@ -149,14 +149,22 @@ def spearman(a, b):
 
 
 def explore(n_train=512, n_val=128, n_candidates=20000, top_k=64, seed=11, steps=3000, n_samples=256,
-            evaluator=None):
+            evaluator=None, rounds=1, surrogate=None):
     """Train on simulated points, rank candidates, re-simulate the top_k and
-    a random top_k; returns a report dict."""
+    a random top_k; returns a report dict.
+
+    With rounds > 1 the search is refined: after each round the re-simulated
+    candidates join the training set, a new surrogate is trained on all of
+    them and the top_k candidates not simulated yet are simulated next.  The
+    random baseline then gets the same budget (rounds * top_k exact
+    simulations).  `evaluator` (an Evaluator) and `surrogate` (a factory
+    taking a seed, default Surrogate) can be replaced."""
     ev = evaluator or Evaluator(n_samples=n_samples)
+    make = surrogate or (lambda sd: Surrogate(seed=sd))
     pts = D.sample_points(seed, n_train + n_val)
     Y = ev.targets(pts)
     X = features(pts)
-    sur = Surrogate()
+    sur = make(1)
     t0 = time.perf_counter()
     losses = sur.fit(X[:n_train], Y[:n_train], steps=steps)
     train_s = time.perf_counter() - t0
@@ -164,24 +172,54 @@ def explore(n_train=512, n_val=128, n_candidates=20000, top_k=64, seed=11, steps
     mae = np.abs(Yv - Y[n_train:]).mean(axis=0)
     rho_val = spearman(objective(Yv[:, 0], Yv[:, 1]), objective(Y[n_train:, 0], Y[n_train:, 1]))
     cand = D.sample_points(seed + 1, n_candidates)
+    Xc = features(cand)
     t0 = time.perf_counter()
-    pred = sur.predict(features(cand))
+    pred = sur.predict(Xc)
     rank_s = time.perf_counter() - t0
     score = objective(pred[:, 0], pred[:, 1])
     top = np.argsort(-score, kind="stable")[:top_k]
-    rnd = np.random.default_rng(seed + 2).choice(n_candidates, size=top_k, replace=False)
+    rnd_all = np.random.default_rng(seed + 2).choice(n_candidates, size=min(n_candidates, rounds * top_k),
+                                                     replace=False)
+    rnd = rnd_all[:top_k]
     Yt = ev.targets([cand[i] for i in top])
     Yr = ev.targets([cand[i] for i in rnd])
     true_top, true_rnd = objective(Yt[:, 0], Yt[:, 1]), objective(Yr[:, 0], Yr[:, 1])
-    return dict(
+    history = [dict(mean=float(true_top.mean()), best=float(true_top.max()),
+                    spearman_pred_vs_true=spearman(score[top], true_top))]
+    chosen, Ych = list(top), [Yt]
+    for r in range(1, rounds):
+        Xr = np.concatenate([X[:n_train], Xc[chosen]])
+        Yrr = np.concatenate([Y[:n_train]] + Ych)
+        sur_r = make(1 + r)
+        sur_r.fit(Xr, Yrr, steps=steps)
+        pr = sur_r.predict(Xc)
+        sc = objective(pr[:, 0], pr[:, 1])
+        sc[chosen] = -np.inf  # simulated already
+        nxt = np.argsort(-sc, kind="stable")[:top_k]
+        Yn = ev.targets([cand[i] for i in nxt])
+        tn = objective(Yn[:, 0], Yn[:, 1])
+        history.append(dict(mean=float(tn.mean()), best=float(tn.max()), spearman_pred_vs_true=spearman(sc[nxt], tn)))
+        chosen += list(nxt)
+        Ych.append(Yn)
+    rep = dict(
         n_train=n_train, n_val=n_val, n_candidates=n_candidates, top_k=top_k, train_steps=steps,
         final_train_loss=losses[-1], val_mae_agreement=float(mae[0]), val_mae_rel_traffic=float(mae[1]),
         val_spearman_objective=rho_val,
         top_true_objective_mean=float(true_top.mean()), random_true_objective_mean=float(true_rnd.mean()),
         top_true_objective_best=float(true_top.max()), random_true_objective_best=float(true_rnd.max()),
         gain_mean=float(true_top.mean() - true_rnd.mean()),
-        spearman_top_pred_vs_true=spearman(score[top], true_top),
-        sims=ev.n_sims, sim_seconds=ev.sim_seconds, seconds_per_sim=ev.sim_seconds / max(ev.n_sims, 1),
-        sim_kernel_launches=ev.launches,
-        train_seconds=train_s, rank_seconds=rank_s,
-        exact_sims_saved=n_candidates - top_k)
+        spearman_top_pred_vs_true=history[0]["spearman_pred_vs_true"],
+        rounds=rounds)
+    if rounds > 1:
+        Ya = ev.targets([cand[i] for i in rnd_all[top_k:]])
+        true_all = np.concatenate([true_rnd, objective(Ya[:, 0], Ya[:, 1])])
+        found = objective(np.concatenate(Ych)[:, 0], np.concatenate(Ych)[:, 1])
+        rep.update(round_history=history, refined_best=float(found.max()),
+                   refined_top_mean=float(np.sort(found)[-top_k:].mean()),
+                   random_best_same_budget=float(true_all.max()),
+                   random_top_mean_same_budget=float(np.sort(true_all)[-top_k:].mean()),
+                   exact_sims_by_search=rounds * top_k)
+    rep.update(sims=ev.n_sims, sim_seconds=ev.sim_seconds, seconds_per_sim=ev.sim_seconds / max(ev.n_sims, 1),
+               sim_kernel_launches=ev.launches, train_seconds=train_s, rank_seconds=rank_s,
+               exact_sims_saved=n_candidates - rounds * top_k)
+    return rep
