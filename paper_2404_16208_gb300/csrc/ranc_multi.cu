@@ -80,7 +80,8 @@ constexpr uint32_t kBlk = 16384;  // one 16 KB block: 128 weight rows x 64 fp16,
 constexpr int kMaxKB = 8;         // axons <= 512
 constexpr int kMaxStagesM = 6;
 constexpr int kSlots = 4;         // accumulators of 128 tensor-memory columns (512 columns)
-constexpr int kClsCapM = 16384;   // items of a CTA whose classes are kept in shared memory
+constexpr int kClsCapM = 16384;   // most items of a CTA whose classes are kept in shared memory
+constexpr int kClsCapMinM = 8192; // fewest: a weight stage is dropped rather than the cache cut below this
 
 // One network of a multi-network handle (device table).
 struct SegDev {
@@ -122,6 +123,7 @@ struct MultiArgs {
     unsigned long long *item_ticks;  // [3 + 2 * n_seg]: updated, deferred (always 0 here), active item-ticks,
                                      // then updated and active item-ticks of each network
     int kbmax;                 // largest A/64 of the handle: operand blocks kept in shared memory
+    int cls_cap;               // items of a CTA whose classes fit the shared-memory cache (at most kClsCapM)
     int stall_test;            // failure-detection tests only: CTA 0's issuer waits for its first weight
                                // block on a barrier armed with a transaction count no copy satisfies
     int dbg_plant;             // debug builds: site whose range checks fail on purpose (0: none)
@@ -212,7 +214,7 @@ __device__ __noinline__ void split_multi(const MultiArgs &a, const int *cost_sh,
     for (int li = tid; li < n_items; li += kThreadsM) {
         const int it = i0 + li, g = it / T;
         const bool act = all_of(g) || stamp_row[it] == cycle;
-        if (n_items <= kClsCapM) cls_sm[li] = act ? 2 : 1;
+        if (n_items <= a.cls_cap) cls_sm[li] = act ? 2 : 1;
         const int s = core_seg[g];
         atomicAdd(&seg_sh[2 * s], 1u);
         if (act) atomicAdd(&seg_sh[2 * s + 1], 1u);
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(kThreadsM, 1) multi_tick_kernel(const __grid_c
     __syncthreads();
     split_multi(a, cost_sh, wsum_sh, cut_sh, cls_sm, seg_sh);
     const int i0 = cut_sh[0], i1 = cut_sh[1], n_items = i1 - i0;
-    const bool cls_cached = n_items <= kClsCapM;
+    const bool cls_cached = n_items <= a.cls_cap;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -737,7 +739,17 @@ Multi *M_of(ranc_sim *s) { return static_cast<Multi *>(s->multi); }
 
 long long grid_m(long long n) { return std::max<long long>(1, std::min<long long>((n + 255) / 256, 8192)); }
 
-size_t smem_for(int kbmax, int stages) { return 1024 + (size_t)(kbmax + stages) * kBlk + 128 + kClsCapM; }
+// Shared memory of a CTA: the operand blocks and weight stages, the table
+// and the class cache, whose capacity takes what is left of 227 KB less
+// 5 KB for the kernel's static shared memory (4.4 KB), at most kClsCapM.
+// (The kernel's shared-memory attribute is raised to the largest of these at
+// create, which fails cleanly if static + dynamic ever exceeded 227 KB.)
+constexpr long long kSmemBudgetM = 227 * 1024 - 5 * 1024;
+int cls_cap_for(int kbmax, int stages) {
+    const long long left = kSmemBudgetM - (1024 + (long long)(kbmax + stages) * kBlk + 128);
+    return (int)std::max(0LL, std::min<long long>(kClsCapM, left) & ~15LL);
+}
+size_t smem_for(int kbmax, int stages) { return 1024 + (size_t)(kbmax + stages) * kBlk + 128 + cls_cap_for(kbmax, stages); }
 
 template <typename VT, int kNR>
 cudaError_t raise_multi_smem(size_t bytes) {
@@ -749,9 +761,8 @@ cudaError_t raise_multi_smem(size_t bytes) {
 bool multi_shape_ok(int A, int N) { return A % 64 == 0 && A >= 64 && A <= 64 * kMaxKB && N % 128 == 0 && N >= 128 && N <= 512; }
 
 int multi_max_stages(int kbmax) {
-    // 227 KB per CTA, less a margin for the kernel's static shared memory.
     int s = kMaxStagesM;
-    while (s > 2 && smem_for(kbmax, s) > 227 * 1024 - 4096) --s;
+    while (s > 2 && cls_cap_for(kbmax, s) < kClsCapMinM) --s;
     return s;
 }
 
@@ -950,7 +961,7 @@ cudaError_t launch_multi_tick(ranc_sim *sim) {
     }
     a.stamp = m->stamp; a.spitch = m->spitch; a.stamp_row = m->stamp + (size_t)(sim->tick & (kRows - 1)) * m->spitch;
     a.sclock = sim->sclock; a.all_active = sim->all_active_ticks > 0; a.core_flags = m->core_flags;
-    a.item_ticks = m->item_ticks; a.kbmax = m->kbmax; a.stall_test = sim->stall_test; a.dbg_plant = sim->dbg_plant;
+    a.item_ticks = m->item_ticks; a.kbmax = m->kbmax; a.cls_cap = cls_cap_for(m->kbmax, m->stages); a.stall_test = sim->stall_test; a.dbg_plant = sim->dbg_plant;
     const int grid = std::min(m->n_sm, a.items);
     const size_t smem = smem_for(m->kbmax, m->stages);
     auto kern = sim->vmode == kVHalf    ? (sim->neg_mode ? multi_tick_kernel<__half, 1> : multi_tick_kernel<__half, 0>)
