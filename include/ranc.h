@@ -262,8 +262,7 @@ int ranc_reset(ranc_sim *sim);
  * samples, stepped `window` ticks, and its output-bus counts are written to
  * counts[s][n_outputs].  A last partial group leaves the unused samples
  * without input and without output.  `mem` says whether `inputs` and `counts`
- * are host (synchronous) or device (stream-ordered) memory; host buffers go
- * through device buffers the handle keeps (inputs at most 256 MB at a time).  The paper streams
+ * are host (synchronous) or device (stream-ordered) memory.  The paper streams
  * images through one network (Table I) and says nothing of sample boundaries;
  * here every sample starts from V = v0, empty schedulers and tick 0. */
 int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n_samples, int32_t t_in, int32_t window,

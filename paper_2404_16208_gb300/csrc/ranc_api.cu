@@ -356,18 +356,6 @@ int ensure_stage(ranc_sim *sim, size_t words) {
     return RANC_OK;
 }
 
-// Device copy of the output counts of a host-memory ranc_run_samples.
-int ensure_counts_dev(ranc_sim *sim, size_t words) {
-    if (words <= sim->counts_cap) return RANC_OK;
-    CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
-    if (sim->counts_dev) cudaFree(sim->counts_dev);
-    sim->counts_dev = nullptr;
-    sim->counts_cap = 0;
-    if (dmalloc(&sim->counts_dev, words) != cudaSuccess) return fail(sim, RANC_ENOMEM, "count buffer");
-    sim->counts_cap = words;
-    return RANC_OK;
-}
-
 int load_inputs_host(ranc_sim *sim, const uint32_t *bits, int n_samples, int n_ticks) {
     const size_t words = (size_t)n_samples * n_ticks * sim->in_words;
     if (words == 0) return load_inputs_dev(sim, nullptr, n_samples, 0);
@@ -911,8 +899,14 @@ static int run_windows_persistent(ranc_sim *sim, const uint32_t *inputs, int n_s
     uint32_t *dev_counts = counts;
     const size_t cwords = (size_t)n_samples * sim->n_outputs;
     if (mem == RANC_MEM_HOST) {
-        const int rc = ensure_counts_dev(sim, cwords);
-        if (rc) return rc;
+        if (cwords > sim->counts_cap) {
+            CUDA_OR_FAIL(sim, cudaStreamSynchronize(sim->stream));
+            if (sim->counts_dev) cudaFree(sim->counts_dev);
+            sim->counts_dev = nullptr;
+            sim->counts_cap = 0;
+            if (dmalloc(&sim->counts_dev, cwords) != cudaSuccess) return fail(sim, RANC_ENOMEM, "count buffer");
+            sim->counts_cap = cwords;
+        }
         dev_counts = sim->counts_dev;
     }
     w.counts = dev_counts;
@@ -1136,37 +1130,12 @@ extern "C" int ranc_run_samples(ranc_sim *sim, const uint32_t *inputs, int32_t n
         int rc = run_windows_persistent(sim, inputs, n_samples, t_in, window, counts, mem);
         if (rc != RANC_ENOTSUP) return rc;  // otherwise fall through to per-tick launches
     }
-    if (sim->path == RANC_PATH_BATCHED) {
-        // The window graph.  With host buffers, each chunk of samples (at most
-        // kHostChunkWords input words, whole groups) is copied into the staging
-        // buffer, run by the graph and its counts copied back.
-        constexpr size_t kHostChunkWords = (size_t)64 << 20;  // 256 MB of inputs
-        int chunk = n_samples;
-        if (mem == RANC_MEM_HOST && per > 0 && (size_t)n_samples * per > kHostChunkWords)
-            chunk = std::max(sim->B, (int)(kHostChunkWords / per) / sim->B * sim->B);
-        int rc = RANC_OK;
-        for (int s0 = 0; s0 < n_samples && rc == RANC_OK; s0 += chunk) {
-            const int ns = std::min(chunk, n_samples - s0);
-            const uint32_t *dev_in = inputs ? inputs + (size_t)s0 * per : nullptr;
-            uint32_t *dev_counts = counts + (size_t)s0 * sim->n_outputs;
-            if (mem == RANC_MEM_HOST) {
-                const size_t words = (size_t)ns * per;
-                if (words && (rc = ensure_stage(sim, words)) != RANC_OK) break;
-                if ((rc = ensure_counts_dev(sim, (size_t)ns * sim->n_outputs)) != RANC_OK) break;
-                if (words) CUDA_OR_FAIL(sim, cudaMemcpyAsync(sim->stage, dev_in, words * 4, cudaMemcpyHostToDevice, sim->stream));
-                dev_in = words ? sim->stage : nullptr;
-                dev_counts = sim->counts_dev;
-            }
-            rc = run_samples_graph(sim, dev_in, ns, t_in, window, dev_counts);
-            if (rc == RANC_OK && mem == RANC_MEM_HOST)
-                CUDA_OR_FAIL(sim, cudaMemcpyAsync(counts + (size_t)s0 * sim->n_outputs, dev_counts,
-                                                  (size_t)ns * sim->n_outputs * 4, cudaMemcpyDeviceToHost, sim->stream));
-        }
+    if (sim->path == RANC_PATH_BATCHED && mem == RANC_MEM_DEVICE) {
+        int rc = run_samples_graph(sim, inputs, n_samples, t_in, window, counts);
         sim->in_override = nullptr;
         sim->n_valid = sim->B;
         sim->in_ticks = 0;  // the window inputs are not kept as the handle's schedule
-        if (rc || mem == RANC_MEM_DEVICE) return rc;
-        return sync_and_check(sim);
+        return rc;
     }
     for (int s0 = 0; s0 < n_samples; s0 += sim->B) {
         const int ns = std::min(sim->B, n_samples - s0);
