@@ -13,8 +13,8 @@ once in one multi-network handle (ranc_create_multi: the design-sweep runner,
 one tick launch for every point of a chunk), train the surrogate with the
 library's own kernels (include/ranc_mlp.h: tensor-core products, bf16
 weights, fp32 accumulation, Adam), score many seeded candidates with it, and
-simulate only the best-ranked ones exactly, again side by side.  The exact simulator stays the
-judge: reported gains compare re-simulated results of the surrogate's choice
+simulate only the best-ranked ones exactly, again side by side.  The exact simulator has the
+last word: reported gains compare re-simulated results of the surrogate's choice
 with an equally sized random choice.  PyTorch only holds device buffers.
 """
 

@@ -65,7 +65,7 @@ def test_refined_search_bookkeeping(rounds):
     searched = ev.seen[n_train + n_val:]
     cand = D.sample_points(6, n_cand)
     search = searched[:k]
-    if rounds > 1:  # round 1's random choice comes right after round 1's search, the rest of it at the end
+    if rounds > 1:  # the first search's random choice follows it; the rest of the random choice comes last
         search = searched[:k] + searched[2 * k:2 * k + (rounds - 1) * k]
     assert len(set(search)) == rounds * k, "a candidate was simulated twice by the search"
     assert all(p in cand for p in search)
