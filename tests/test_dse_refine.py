@@ -93,3 +93,9 @@ def test_refined_search_finds_the_top_of_a_learnable_objective():
     truth = dse.objective(*true_targets(cand).T)
     assert rep["refined_best"] > rep["random_best_same_budget"]
     assert rep["refined_best"] >= np.sort(truth)[-5]  # among the five best candidates
+
+
+def test_column_features_equal_the_points_own():
+    """The surrogate's column-wise feature matrix equals Point.features() row by row."""
+    pts = D.sample_points(3, 500) + [D.NOMINAL]
+    np.testing.assert_array_equal(dse.features(pts), np.stack([p.features() for p in pts]))
