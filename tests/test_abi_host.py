@@ -75,6 +75,37 @@ def test_debug_library_exports_the_same_symbols(ranc):
             assert hasattr(lib, name), (header, name)
 
 
+def header_constants():
+    """Every integer constant of the headers: #define NAME value and enum members."""
+    out = {}
+    for h in ("ranc.h", "ranc_xbar.h", "ranc_mlp.h"):
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", h)).read(), flags=re.S)
+        for name, val in re.findall(r"#define\s+(RANC_\w+)\s+\(?(-?\d+)\)?", text):
+            out[name] = int(val)
+        for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+            for name, val in re.findall(r"(RANC_\w+)\s*=\s*(-?\d+)", body):
+                out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_headers(ranc):
+    """The binding's and the workload generator's copies of the header constants
+    (return codes, paths, buffer kinds, potential formats, crossbar forms,
+    destination kinds, negative-threshold modes, counter count) are the C values."""
+    consts = header_constants()
+    for name in ("RANC_OK", "RANC_EINVAL", "RANC_ENOMEM", "RANC_ECUDA", "RANC_ETIMEOUT", "RANC_ESTATE",
+                 "RANC_PATH_PLAIN", "RANC_PATH_BATCHED", "RANC_MEM_HOST", "RANC_MEM_DEVICE",
+                 "RANC_POTENTIAL_INT32", "RANC_POTENTIAL_INT16", "RANC_POTENTIAL_FP16",
+                 "RANC_XBAR_F16_FOLDED", "RANC_XBAR_F8_PER_TYPE", "RANC_XBAR_I8_MMA_SYNC"):
+        assert getattr(ranc, name) == consts[name], name
+    from ranc_workloads import nets as NT
+    assert (NT.KIND_NONE, NT.KIND_CORE, NT.KIND_OUTPUT) == (consts["RANC_DEST_NONE"], consts["RANC_DEST_CORE"],
+                                                             consts["RANC_DEST_OUTPUT"])
+    assert (NT.NEG_SATURATE, NT.NEG_RESET) == (consts["RANC_NEG_SATURATE"], consts["RANC_NEG_RESET"])
+    assert len(ranc.COUNTER_NAMES) == consts["RANC_N_COUNTERS"]
+    assert consts["RANC_ROWS"] == 16
+
+
 def test_struct_layout_matches_c(tmp_path, ranc):
     exe = tmp_path / "abi_probe"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_probe.c"),
